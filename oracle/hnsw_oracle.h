@@ -1,0 +1,135 @@
+/*
+ * hnsw_oracle.h -- the ORACLE: a plain, slow, single-threaded CPU restatement of
+ * Hierarchical NSW (Malkov & Yashunin, arXiv:1603.09320), Algorithms 1-5.
+ *
+ * This is TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load or call it.  It shares no
+ * code, header, table or helper with the CUDA library under
+ * paper_1603_09320_gb300/; the only interface the two have in common is the
+ * serialised graph format described below, which each side reads and writes
+ * with its own code.
+ *
+ * Precision: distances are accumulated in fp64 from the fp32 coordinates
+ * (the paper fixes no precision).
+ *
+ * Readings of points the paper leaves open (each is also listed in the design
+ * notes of the repository):
+ *  - Ties: every "nearest"/"furthest" comparison orders elements by the key
+ *    (distance, id), lexicographically.  Alg. 2's break test is key(c) > key(f)
+ *    and its insertion test is key(e) < key(f) or |W| < ef.
+ *  - Alg. 4, the acceptance test ("e is closer to q compared to any element
+ *    from R"): accept e iff dist(e,q) < dist(e,r) for every r in R (strict;
+ *    R empty accepts).
+ *  - keepPrunedConnections defaults to false, extendCandidates to false
+ *    (Section 4, text after Alg. 5).
+ *  - Levels: l = floor(-ln(u) * mL) with u in (0,1] supplied by the caller,
+ *    one u per element in id order (Alg. 1, line 4).
+ *  - The first element becomes the enter point with its drawn level and no
+ *    links.  The enter point changes only when l > L (Alg. 1, line 18).
+ *  - Alg. 1, line 17 "ep <- W": all elements of W seed the next layer's search.
+ *  - No self links and no duplicate links are ever stored.
+ *  - Alg. 5 with ef < K runs the layer-0 search with ef' = max(ef, K); missing
+ *    results (fewer than K reachable elements) are reported as id 0xFFFFFFFF
+ *    and distance +inf.
+ *  - Cosine distance is 1 - <q,x>; vectors are expected unit-normalised
+ *    ("equivalent to L2 after normalization", Section 5.2).
+ *
+ * Serialised graph format "HNSWGB01" (little-endian), shared with the
+ * library's own reader/writer:
+ *   header, 128 bytes:
+ *     0  char[8] magic "HNSWGB01"   8  u32 version (1)      12 u32 metric (0 L2SQ, 1 COSINE)
+ *     16 u64 N                      24 u32 d                 28 u32 M
+ *     32 u32 Mmax                   36 u32 Mmax0             40 u32 maxlevel (level of ep)
+ *     44 u32 ep (0xFFFFFFFF if N=0) 48 u32 flags (bit0 heuristic, bit1 extendCandidates,
+ *                                                bit2 keepPrunedConnections)
+ *     52 u32 efConstruction         56 f64 mL                64 u64 n_upper_rows
+ *     72 u64 checksum (64-bit FNV-1a over every payload byte)  80..127 zero
+ *   payload, in this order, each section starting on a 16-byte boundary
+ *   (zero padding between sections):
+ *     f32 data[N][d]
+ *     u8  level[N]
+ *     u32 nbr0[N][Mmax0]             layer-0 lists, valid ids first, then 0xFFFFFFFF
+ *     u32 nbrU[n_upper_rows][Mmax]   for each element in id order, one row per
+ *                                    layer 1..level[i]; same padding rule
+ */
+#ifndef HNSW_ORACLE_H
+#define HNSW_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_NONE 0xFFFFFFFFu
+
+typedef struct orc_graph orc_graph;
+
+typedef struct {
+    uint64_t n_dist;   /* distance evaluations (every call of the distance function) */
+    uint64_t n_hops0;  /* elements extracted from C and expanded on layer 0 */
+    uint64_t n_hopsU;  /* elements expanded on layers >= 1 */
+} orc_stats;
+
+/* New empty graph over N elements of dimension d (data copied, fp32 row-major).
+ * metric 0 = squared L2, 1 = cosine (1 - <q,x>). Returns NULL on bad args. */
+orc_graph* orc_new(const float* data, uint64_t N, uint32_t d, int metric,
+                   uint32_t M, uint32_t Mmax, uint32_t Mmax0, uint32_t efC, double mL,
+                   int heuristic, int extend_candidates, int keep_pruned);
+void orc_free(orc_graph* g);
+
+/* Alg. 1, line 4: l = floor(-ln(u) * mL). */
+int orc_level_from_u(double u, double mL);
+
+/* Alg. 1: insert element `id` (its vector is row `id` of the data) at level l. */
+int orc_insert(orc_graph* g, uint32_t id, int level);
+
+/* Inserts elements 0..N-1 in order, element i at level orc_level_from_u(u[i], mL). */
+int orc_build(orc_graph* g, const double* u);
+
+/* Alg. 5: K nearest of q; ids/dists have K slots; missing -> ORC_NONE/+inf. */
+int orc_knn_search(const orc_graph* g, const float* q, int K, int ef,
+                   uint32_t* ids, double* dists, orc_stats* st);
+
+/* Alg. 2 on layer lc from enter points ep[0..n_ep); returns |W| and writes W
+ * sorted ascending by key into out_ids/out_dists (capacity >= ef). */
+int orc_search_layer(const orc_graph* g, const float* q, const uint32_t* ep, int n_ep,
+                     int ef, int lc, uint32_t* out_ids, double* out_dists, orc_stats* st);
+
+/* Steepest-descent form of Alg. 2 with ef = 1 (used to check the lemma that the
+ * two coincide under key order): returns the local minimum reached from ep. */
+uint32_t orc_greedy_layer(const orc_graph* g, const float* q, uint32_t ep, int lc, orc_stats* st);
+
+/* Alg. 3 / Alg. 4 as standalone routines over candidate lists (base is a vector
+ * `base` with optional element id base_id to exclude; cand ids refer to data rows).
+ * Writes at most M selected ids (in selection order) and returns their number. */
+int orc_select_simple(const orc_graph* g, const float* base, const uint32_t* cand,
+                      int n_cand, int M, uint32_t* out);
+int orc_select_heuristic(const orc_graph* g, const float* base, uint32_t base_id,
+                         const uint32_t* cand, int n_cand, int M, int lc,
+                         int extend_candidates, int keep_pruned, uint32_t* out);
+
+/* Distance between a vector and data row i (fp64). */
+double orc_dist_to(const orc_graph* g, const float* q, uint32_t i);
+
+/* Inspection. */
+uint64_t orc_n(const orc_graph* g);
+int orc_level(const orc_graph* g, uint32_t i);
+uint32_t orc_enter_point(const orc_graph* g);
+int orc_max_level(const orc_graph* g);
+int orc_neighbors(const orc_graph* g, uint32_t i, int lc, uint32_t* out, int cap);
+
+/* Serialisation (format above). orc_blob_size gives the exact byte count. */
+uint64_t orc_blob_size(const orc_graph* g);
+int orc_save_blob(const orc_graph* g, void* out, uint64_t cap);
+orc_graph* orc_load_blob(const void* blob, uint64_t bytes, int* err);
+
+/* Exact k-NN by scanning all N rows (fp64 distances, key order). */
+void orc_brute_force(const float* data, uint64_t N, uint32_t d, int metric,
+                     const float* q, int K, uint32_t* ids, double* dists);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
