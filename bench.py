@@ -1,0 +1,486 @@
+"""Benchmark of batched HNSW K-NN search (Alg. 5) on one GB300.
+
+Workload (default): SIFT-shaped 1M x 128 integer-valued vectors, squared L2,
+M=16, Mmax0=32, efConstruction=200, 10,000 queries from the same mixture,
+k=10.  Metric: queries/s at recall@10 >= 0.95 (recall against exact fp64
+k-NN), for the chosen form (reduced-precision storage + exact fp32 rerank)
+with the plain fp32 form reported beside it, and the achieved fraction of the
+HBM roofline of the search kernel.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    torchrun --nproc-per-node N bench.py --gpus N ...   (replicas: each rank
+        searches its own 10,000 queries on its own copy of the index)
+
+One step = one launch of the search over the whole 10,000-query batch with
+queries, graph and outputs resident in device memory.  L2 is flushed (a 512 MB
+device write) between timed steps; step time is the CUDA-event time of the
+search call on its stream.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10≥0.95, 1M×128, chosen vs plain GPU form; % of HBM-gather roofline"
+EF_SWEEP = [10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 400]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-base", type=int, default=1_000_000)
+    ap.add_argument("--n-queries", type=int, default=10_000)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--target-recall", type=float, default=0.95)
+    ap.add_argument("--threads", type=int, default=0, help="builder threads (0: all)")
+    ap.add_argument("--forms", default="f32,bf16r,fp8r")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--profile-once", action="store_true", help="one warm step of the chosen form, then exit")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+def workload(args):
+    from paper_1603_09320_gb300 import synth
+    X = synth.base("sift", args.n_base)
+    Q = synth.queries("sift", args.n_queries)
+    u = synth.level_uniforms("sift", args.n_base)
+    return X, Q, u
+
+
+def graph_blob(args, X, u, log):
+    """Builds (or reuses within this machine) the graph with the host builder."""
+    from paper_1603_09320_gb300 import graphs
+    return graphs.build_or_load("sift", args.n_base, threads=args.threads, X=X, log=log)
+
+
+def ground_truth(X, Q, k, device):
+    """Exact k-NN: fp32 shortlist of 32 on the GPU (exact for these integer
+    coordinates, all sums < 2^24), then fp64 rescoring on the host by key
+    (distance, id)."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Xd = torch.from_numpy(X).to(device)
+    xn = (Xd * Xd).sum(1)
+    m = 32
+    out = np.zeros((Q.shape[0], k), dtype=np.int64)
+    for s in range(0, Q.shape[0], 1000):
+        q = torch.from_numpy(Q[s:s + 1000]).to(device)
+        d = xn[None, :] - 2.0 * (q @ Xd.T)
+        cand = torch.topk(d, m, dim=1, largest=False).indices.cpu().numpy()
+        for i in range(cand.shape[0]):
+            c = cand[i]
+            ex = ((X[c].astype(np.float64) - Q[s + i].astype(np.float64)) ** 2).sum(1)
+            order = np.lexsort((c, ex))[:k]
+            out[s + i] = c[order]
+    del Xd
+    torch.cuda.empty_cache()
+    return out
+
+
+def recall_at(ids, gt):
+    ids = ids.astype(np.int64)
+    hits = 0
+    for i in range(gt.shape[0]):
+        hits += len(set(ids[i].tolist()) & set(gt[i].tolist()))
+    return hits / gt.size
+
+
+# --------------------------------------------------------------------------
+# GPU side
+# --------------------------------------------------------------------------
+FORMS = {  # name: (storage, keep fp32, rerank)
+    "f32": ("f32", False, False),
+    "bf16r": ("bf16", True, True),
+    "fp8r": ("fp8", True, True),
+}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev_index, enabled=True):
+        self.p = None
+        self.path = None
+        if not enabled:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_forms(args, blob, Q, gt, log):
+    import torch
+    from paper_1603_09320_gb300 import hnsw
+    dev = torch.device("cuda", torch.cuda.current_device())
+    q = torch.from_numpy(Q).to(dev)
+    n, k = Q.shape[0], args.k
+    ids = torch.empty((n, k), dtype=torch.int32, device=dev)
+    ds = torch.empty((n, k), dtype=torch.float32, device=dev)
+    st = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    res = {}
+    indexes = {}
+    for name in args.forms.split(","):
+        storage, keep, rerank = FORMS[name]
+        ix = hnsw.Index(blob, storage, keep_fp32=keep)
+        indexes[name] = ix
+        sweep = []
+        chosen = None
+        for ef in EF_SWEEP:
+            if ef < k:
+                continue
+            ix.search_into(q, k, ef, ids, ds, st, rerank=rerank)
+            torch.cuda.synchronize()
+            r = recall_at(ids.cpu().numpy().view(np.uint32), gt)
+            sweep.append((ef, r))
+            if r >= args.target_recall:
+                chosen = ef
+                break
+        res[name] = {"storage": storage, "rerank": rerank, "sweep": sweep, "ef": chosen}
+        log(f"form {name}: sweep {sweep}")
+    return res, indexes, (q, ids, ds, st)
+
+
+def time_form(args, ix, ef, rerank, bufs, steps, warmup, flush):
+    import torch
+    q, ids, ds, st = bufs
+    k = args.k
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        ix.search_into(q, k, ef, ids, ds, st, rerank=rerank)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(s)
+        ix.search_into(q, k, ef, ids, ds, st, rerank=rerank)
+        e1.record(s)
+    torch.cuda.synchronize()
+    times = [e0.elapsed_time(e1) for e0, e1 in evs]
+    stats = st.cpu().numpy().view(np.uint32)
+    return times, stats
+
+
+def algorithmic_bytes(info, stats, k, ef, rerank, d):
+    """Bytes one launch must move (per-query counters of the kernel):
+    gathered rows (+ fp8 scale), layer-0 and upper adjacency rows (ids, plus
+    the 4-byte upper offset), the exact rerank rows, the query and results."""
+    row = info.row_bytes + (4 if info.storage == 2 else 0)
+    s0 = (info.Mmax0 + 3) // 4 * 4 * 4
+    sU = (info.Mmax + 3) // 4 * 4 * 4 + 4
+    efp = max(ef, k)
+    n_eval = stats[:, 0].astype(np.float64)
+    n_exp0 = stats[:, 1].astype(np.float64)
+    n_up = stats[:, 2].astype(np.float64)
+    per_q = n_eval * row + n_exp0 * s0 + n_up * sU + d * 4 + k * 8
+    if rerank:
+        per_q = per_q + efp * ((d + 3) // 4 * 4 * 4)
+    return float(per_q.sum()), {"n_eval": float(n_eval.mean()), "n_exp0": float(n_exp0.mean()),
+                                "n_stepU": float(n_up.mean()), "bytes_per_query": float(per_q.mean())}
+
+
+def e2e_host(args, ix, ef, rerank, Q, steps):
+    """The same search through the C ABI with pinned HOST buffers: the call
+    copies the queries in, searches and copies ids/dists back each step."""
+    import torch
+    n, k = Q.shape[0], args.k
+    qh = torch.from_numpy(Q).pin_memory()
+    ih = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    dh = torch.empty((n, k), dtype=torch.float32).pin_memory()
+    ix.search_into(qh, k, ef, ih, dh, None, rerank=rerank)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        ix.search_into(qh, k, ef, ih, dh, None, rerank=rerank)  # synchronous for host buffers
+        t.append(time.perf_counter() - t0)
+    return n / statistics.mean(t), int(qh.numel() * 4), int(ih.numel() * 4 + dh.numel() * 4)
+
+
+def load_traffic(kernel_tag):
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    src = open(os.path.join(ROOT, "paper_1603_09320_gb300", "csrc", "search.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    if not os.path.exists(path):
+        return None, sha
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None, sha
+    e = d.get(kernel_tag)
+    if not e or e.get("search_cu_sha") != sha:
+        return None, sha
+    return e.get("traffic_bytes_per_launch"), sha
+
+
+# --------------------------------------------------------------------------
+# CPU oracle leg
+# --------------------------------------------------------------------------
+def oracle_leg(blob, Q, gt, k, ef, seconds):
+    """The oracle (single-threaded, as it stands) on a bounded sample."""
+    from oracle import oracle as O
+    g = O.Graph.from_blob(blob)
+    t0 = time.perf_counter()
+    done = 0
+    ids = []
+    n_dist = []
+    while done < Q.shape[0] and time.perf_counter() - t0 < seconds:
+        r = g.knn_search(Q[done], k, ef, stats=True)
+        ids.append(r[0])
+        n_dist.append(r[2].n_dist)
+        done += 1
+    dt = time.perf_counter() - t0
+    rec = recall_at(np.array(ids), gt[:done])
+    return {"value": done / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} of the {Q.shape[0]} queries, ef={ef}, single thread, {dt:.1f}s",
+            "recall": rec, "n_dist_mean": float(np.mean(n_dist))}, np.array(ids)
+
+
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    def log(msg):
+        if rank == 0:
+            print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+    if args.impl == "reference":
+        return reference_arm(args, rank, world, log)
+
+    import torch
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    from paper_1603_09320_gb300 import build as B
+    from paper_1603_09320_gb300 import hnsw
+    if rank == 0:
+        B.build()
+    if pg:
+        pg.barrier()
+    hnsw.lib()
+    X, Q, u = workload(args)
+    build_s = None
+    if rank == 0:
+        blob, build_s = graph_blob(args, X, u, log)
+    if pg:
+        pg.barrier()
+    if rank != 0:
+        blob, _ = graph_blob(args, X, u, log)
+    gt = ground_truth(X, Q, args.k, torch.device("cuda", local))
+    forms, indexes, bufs = run_forms(args, blob, Q, gt, log)
+    ok = {n: f for n, f in forms.items() if f["ef"] is not None}
+    if "f32" not in ok:
+        raise SystemExit("plain form never reached the target recall")
+    # chosen form: the fastest reduced-precision form at the target recall
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    timing = {}
+    for name, f in ok.items():
+        t, stats = time_form(args, indexes[name], f["ef"], f["rerank"], bufs, max(3, args.steps // 2), 2, flush)
+        timing[name] = statistics.mean(t)
+    cands = [n for n in ok if n != "f32"] or ["f32"]
+    chosen = min(cands, key=lambda n: timing[n])
+    fc = ok[chosen]
+    if args.profile_once:
+        indexes[chosen].search_into(bufs[0], args.k, fc["ef"], bufs[1], bufs[2], bufs[3], rerank=fc["rerank"])
+        torch.cuda.synchronize()
+        return
+    # ---- timed region ----------------------------------------------------
+    clocks = Clocks(local, enabled=not args.no_clocks and rank == 0)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    times, stats = time_form(args, indexes[chosen], fc["ef"], fc["rerank"], bufs, args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    if pg:
+        t = torch.tensor([ms], dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    n = Q.shape[0]
+    value = n * world / (ms / 1e3)
+    # plain form beside it
+    tp, stats_p = time_form(args, indexes["f32"], ok["f32"]["ef"], False, bufs, args.steps, args.warmup, flush)
+    ms_p = statistics.mean(tp)
+    info = indexes[chosen].info
+    ab, cnt = algorithmic_bytes(info, stats, args.k, fc["ef"], fc["rerank"], X.shape[1])
+    ab_p, cnt_p = algorithmic_bytes(indexes["f32"].info, stats_p, args.k, ok["f32"]["ef"], False, X.shape[1])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved = ab / (ms / 1e3) / 1e9
+    achieved_p = ab_p / (ms_p / 1e3) / 1e9
+    traffic, sha = load_traffic(f"hnsw_search_kernel:{chosen}")
+    e2e_v, h2d, d2h = e2e_host(args, indexes[chosen], fc["ef"], fc["rerank"], Q, max(3, args.steps // 2))
+    if rank != 0:
+        return
+    cpu, _ = oracle_leg(blob, Q, gt, args.k, ok["f32"]["ef"], args.cpu_seconds)
+    out = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": f"SIFT-shaped {n}-query batch over {args.n_base}x{X.shape[1]} integer-valued vectors, "
+                        "squared L2, M=16 Mmax0=32 efC=200, k=10",
+            "form": chosen, "storage": fc["storage"], "rerank": fc["rerank"], "ef": fc["ef"],
+            "recall_at_10": dict(fc["sweep"])[fc["ef"]],
+            "plain_f32": {"ef": ok["f32"]["ef"], "qps": round(n * world / (ms_p / 1e3), 1),
+                          "ms_per_step": round(ms_p, 4), "recall_at_10": dict(ok["f32"]["sweep"])[ok["f32"]["ef"]],
+                          "roofline_frac": round(achieved_p / peak, 4), "achieved_gbs": round(achieved_p, 1),
+                          "counters": cnt_p},
+            "forms": {k2: {"ef": v["ef"], "sweep": v["sweep"], "ms_per_step": round(timing.get(k2, 0), 4)}
+                      for k2, v in forms.items()},
+            "l2": "flushed between timed steps (512 MB device write, outside the events)",
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "build_seconds": build_s,
+            "counters": cnt,
+        },
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "kernel": f"hnsw_search_kernel ({chosen})", "search_cu_sha": sha},
+        "cpu_baseline": {k2: v for k2, v in cpu.items() if k2 in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": round(e2e_v, 1), "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    out["cpu_baseline"]["recall_at_10"] = cpu["recall"]
+    out["cpu_baseline"]["oracle_n_dist_mean"] = cpu["n_dist_mean"]
+    print(json.dumps(out), flush=True)
+
+
+def reference_arm(args, rank, world, log):
+    """The oracle, as it stands, on the host cores: same metric on bounded
+    samples of the same workload (one step = a sample of queries)."""
+    if rank != 0:
+        return
+    from paper_1603_09320_gb300 import build as B
+    B.build()
+    from oracle import oracle as O
+    O.build()
+    X, Q, u = workload(args)
+    blob, _ = graph_blob(args, X, u, log)
+    g = O.Graph.from_blob(blob)
+    S = 64  # queries per step
+    sample = Q[: S * (args.steps + args.warmup + 4)]
+    from oracle.oracle import brute_force  # noqa: F401  (exact k-NN of the sample)
+    gt = exact_knn_numpy(X, sample, args.k)
+    # smallest ef reaching the target recall on the sweep sample
+    ef_ok = None
+    for ef in EF_SWEEP:
+        if ef < args.k:
+            continue
+        ids = np.array([g.knn_search(sample[i], args.k, ef)[0] for i in range(4 * S)])
+        if recall_at(ids, gt[:4 * S]) >= args.target_recall:
+            ef_ok = ef
+            break
+    ef_ok = ef_ok or EF_SWEEP[-1]
+    times = []
+    for s in range(args.warmup + args.steps):
+        qs = sample[(4 + s) * S:(5 + s) * S] if (5 + s) * S <= sample.shape[0] else sample[:S]
+        t0 = time.perf_counter()
+        for i in range(qs.shape[0]):
+            g.knn_search(qs[i], args.k, ef_ok)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = statistics.mean(times) * 1e3
+    value = S / (ms / 1e3)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"SIFT-shaped {args.n_base}x128, k=10, oracle search at ef={ef_ok} "
+                               f"(recall target {args.target_recall})", "queries_per_step": S},
+        "cpu_baseline": {"value": round(value, 2), "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{S} queries per step, single thread"},
+        "e2e": {"value": round(value, 2), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def exact_knn_numpy(X, Q, k):
+    """Exact fp64 k-NN of a small query sample on the host (key order)."""
+    x64 = X.astype(np.float64)
+    xn = (x64 * x64).sum(1)
+    out = np.zeros((Q.shape[0], k), dtype=np.int64)
+    for i in range(Q.shape[0]):
+        q = Q[i].astype(np.float64)
+        d = xn - 2.0 * (x64 @ q) + q @ q
+        c = np.argpartition(d, 64)[:64]
+        ex = ((X[c].astype(np.float64) - q) ** 2).sum(1)
+        out[i] = c[np.lexsort((c, ex))[:k]]
+    return out
+
+
+if __name__ == "__main__":
+    main()

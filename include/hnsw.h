@@ -1,0 +1,188 @@
+/*
+ * hnsw.h -- C ABI of the GB300 batched HNSW search library (libhnsw_gb300.so).
+ *
+ * Hierarchical Navigable Small World graphs (Malkov & Yashunin,
+ * arXiv:1603.09320).  The library builds the multilayer graph on the host
+ * (Alg. 1 INSERT with Alg. 4 SELECT-NEIGHBORS-HEURISTIC, multi-threaded as in
+ * Section 4.1) and answers batches of K-NN queries on one GPU (Alg. 5
+ * K-NN-SEARCH: greedy ef=1 descent through layers L..1 followed by the
+ * ef-bounded SEARCH-LAYER of Alg. 2 on layer 0), in hand-written sm_103a
+ * CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *  - Return an hnsw_status; no C++ exception crosses the ABI.  On failure,
+ *    hnsw_last_error() gives a message for the calling thread.
+ *  - The caller owns query and output buffers; the library owns the memory of
+ *    an index (device memory allocated by hnsw_upload_index, freed by
+ *    hnsw_free_index) and of blobs it returns (freed by hnsw_free_blob).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *  - Element ids are uint32; 0xFFFFFFFF (HNSW_NO_ID) marks "no element".
+ *  - Distances are squared L2, or cosine distance 1 - <q,x> on unit vectors
+ *    (Section 5.2: cosine similarity is L2 after normalisation).
+ *  - Keys (distance, id) order every comparison, lexicographically; this makes
+ *    a result a deterministic function of the graph and the distances.
+ */
+#ifndef HNSW_GB300_H
+#define HNSW_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HNSW_ABI_VERSION 1
+#define HNSW_NO_ID 0xFFFFFFFFu
+
+typedef enum {
+    HNSW_OK = 0,
+    HNSW_EINVAL = 1,   /* bad argument: null pointer, k <= 0, ef < 1, n < 0, size limits */
+    HNSW_ENOMEM = 2,   /* host or device allocation failed */
+    HNSW_ECUDA = 3,    /* a CUDA call or kernel launch failed (message has the CUDA error) */
+    HNSW_ECORRUPT = 4, /* a graph blob failed validation (magic, checksum, links, levels) */
+    HNSW_ETIMEOUT = 5, /* a bounded device-side wait ran out */
+    HNSW_EBUSY = 6     /* resource in use (e.g. server queue full) */
+} hnsw_status;
+
+typedef enum { HNSW_L2SQ = 0, HNSW_COSINE = 1 } hnsw_metric;
+
+/* Storage type of the vectors on the device.  F32 is exact.  BF16 and F16
+ * are round-to-nearest-even from fp32; FP8E4M3 stores code = RNE(x / s_x)
+ * with a per-vector fp32 scale s_x = max_i |x_i| / 448 (saturating).
+ * Distances are always accumulated in fp32 from the dequantised values. */
+typedef enum { HNSW_F32 = 0, HNSW_BF16 = 1, HNSW_FP8E4M3 = 2, HNSW_F16 = 3 } hnsw_dtype;
+
+typedef struct hnsw_index hnsw_index;
+
+/* ------------------------------------------------------------------------ */
+/* Host-side graph construction                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Construction parameters (Alg. 1 inputs; Mmax0 from Section 4.1, where 2*M is
+ * recommended).  mL is the level normalisation (1/ln M recommended). */
+typedef struct {
+    uint32_t M;                 /* links made per inserted element (Alg. 1 line 10) */
+    uint32_t Mmax;              /* cap on links per element on layers >= 1 */
+    uint32_t Mmax0;             /* cap on layer 0 */
+    uint32_t ef_construction;   /* beam width of SEARCH-LAYER during insertion */
+    double mL;                  /* level normalisation factor */
+    int32_t heuristic;          /* 1: Alg. 4, 0: Alg. 3 */
+    int32_t extend_candidates;  /* Alg. 4 flag */
+    int32_t keep_pruned;        /* Alg. 4 flag */
+    int32_t n_threads;          /* <= 0: all hardware threads */
+} hnsw_build_params;
+
+/* Builds the HNSW graph of `data` (fp32 row-major [N][d], host memory) by
+ * concurrent insertion of elements 0..N-1 (Alg. 1; Section 4.1: parallel
+ * construction with per-element locks and one lock for the enter point).
+ * Element i gets level floor(-ln(level_u[i]) * mL) (Alg. 1 line 4); level_u
+ * holds N host doubles in (0,1].  With n_threads = 1 elements are inserted in
+ * id order, which is exactly Alg. 1 applied sequentially.
+ * On success *out_blob receives a library-allocated graph blob in the
+ * "HNSWGB01" format (below) of *out_bytes bytes; free it with hnsw_free_blob.
+ * Errors: HNSW_EINVAL (null pointers, d = 0, N >= 2^31, M > Mmax or Mmax0,
+ * Mmax0 > 64, mL <= 0), HNSW_ENOMEM. */
+hnsw_status hnsw_build(const float* data, uint64_t N, uint32_t d, hnsw_metric metric,
+                       const hnsw_build_params* params, const double* level_u,
+                       void** out_blob, uint64_t* out_bytes);
+void hnsw_free_blob(void* blob);
+
+/* Graph blob format "HNSWGB01" (little-endian), the interface shared with
+ * other producers of graphs (e.g. test tools):
+ *   header, 128 bytes:
+ *     0 char[8] "HNSWGB01"  8 u32 version=1  12 u32 metric  16 u64 N  24 u32 d
+ *     28 u32 M  32 u32 Mmax  36 u32 Mmax0  40 u32 maxlevel  44 u32 enter point
+ *     48 u32 flags (bit0 heuristic, bit1 extendCandidates, bit2 keepPruned)
+ *     52 u32 efConstruction  56 f64 mL  64 u64 n_upper_rows
+ *     72 u64 FNV-1a-64 of all payload bytes   80..127 zero
+ *   payload, each section 16-byte aligned (zero padded):
+ *     f32 data[N][d]; u8 level[N]; u32 nbr0[N][Mmax0];
+ *     u32 nbrU[n_upper_rows][Mmax] (element-major, layers 1..level[i]);
+ *   lists hold their valid ids first, then 0xFFFFFFFF. */
+
+/* ------------------------------------------------------------------------ */
+/* Device index                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Validates a graph blob (host memory) and packs it into device memory:
+ * vectors as `storage` rows padded to a multiple of 16 bytes, the layer-0
+ * adjacency [N][Mmax0], the upper-layer rows with a per-element offset, and
+ * the enter point and top level.  keep_fp32_for_rerank additionally keeps
+ * an fp32 copy of the vectors for hnsw_search_ex's exact rerank.
+ * The copy is issued on `stream`; the call synchronises it before returning.
+ * Errors: HNSW_EINVAL, HNSW_ECORRUPT (blob fails validation: magic, version,
+ * size, checksum, ids out of range, self or duplicate links, links to
+ * elements absent from a layer, enter point not on the top level),
+ * HNSW_ENOMEM, HNSW_ECUDA. */
+hnsw_status hnsw_upload_index(const void* graph_blob, uint64_t blob_bytes, hnsw_dtype storage,
+                              int keep_fp32_for_rerank, void* stream, hnsw_index** out);
+
+hnsw_status hnsw_free_index(hnsw_index* index);
+
+typedef struct {
+    uint64_t N;
+    uint32_t d, d_pad, row_bytes;
+    int32_t metric, storage, has_fp32;
+    uint32_t M, Mmax, Mmax0;
+    int32_t max_level;
+    uint32_t enter_point;
+    uint64_t n_upper_rows;
+    uint64_t device_bytes;
+} hnsw_index_info;
+
+hnsw_status hnsw_get_index_info(const hnsw_index* index, hnsw_index_info* out);
+
+/* ------------------------------------------------------------------------ */
+/* Search                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Alg. 5 K-NN-SEARCH for n queries (fp32 row-major [n][d]; for COSINE the
+ * queries must be unit-normalised).  The layer-0 beam uses ef' = max(ef, k).
+ * Writes out_ids[n][k] and out_dists[n][k] sorted ascending by (dist, id);
+ * slots beyond the reachable elements hold HNSW_NO_ID / +inf.
+ * Pointers may be host or device memory (detected per pointer).  With only
+ * device pointers the call is asynchronous on `stream`; if any pointer is
+ * host memory the call copies through library-owned device buffers and
+ * synchronises `stream` before returning.
+ * Errors: HNSW_EINVAL (null index/pointers with n > 0, k < 1, ef < 1, n < 0,
+ * k > 1024, ef' > the kernel limit 1024), HNSW_ECUDA. */
+hnsw_status hnsw_search(hnsw_index* index, const float* queries, int64_t n, int32_t k, int32_t ef,
+                        uint32_t* out_ids, float* out_dists, void* stream);
+
+/* Per-query counters (the paper's cost measure is the number of distance
+ * computations, Section 5.1). */
+typedef struct {
+    uint32_t n_eval;    /* distance evaluations on all layers */
+    uint32_t n_exp0;    /* layer-0 expansions (elements taken from C) */
+    uint32_t n_stepU;   /* elements expanded on layers >= 1 */
+    uint32_t flags;     /* bit0: visited set overflowed (lossy, results unaffected);
+                           bit1: stopped early by the learned stop */
+} hnsw_query_stats;
+
+typedef struct {
+    int32_t k;
+    int32_t ef;
+    int32_t rerank;          /* 1: recompute fp32 distances of all ef' final candidates
+                                from the fp32 copy and return the top k of those */
+    int32_t visited_log2;    /* log2 of visited-set slots per query, 0 = automatic */
+    float stop_threshold;    /* learned stop: stop when sigmoid(MLP) > threshold; >= 1 disables */
+    int32_t stop_period;     /* learned stop: evaluate every stop_period expansions */
+    int32_t reserved[2];
+} hnsw_search_params;
+
+/* hnsw_search with the options above and optional per-query counters
+ * (stats may be NULL; host or device memory, [n]). */
+hnsw_status hnsw_search_ex(hnsw_index* index, const hnsw_search_params* params,
+                           const float* queries, int64_t n, uint32_t* out_ids, float* out_dists,
+                           hnsw_query_stats* stats, void* stream);
+
+/* Thread-local message describing the last failure of this thread. */
+const char* hnsw_last_error(void);
+
+int hnsw_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,73 @@
+// index.cuh -- the device-resident layout of one HNSW index and the host
+// object that owns it.
+//
+// Device layout (Section 4.2.3 sizes the links at (Mmax0 + mL*Mmax) * 4 bytes
+// per element; ids are 4-byte unsigned integers):
+//   vec    [N][row_chunks]  16-byte chunks; storage dtype, row zero padded
+//   scale  [N]              fp32 per-row scale (FP8E4M3 storage only)
+//   vec32  [N][row_chunks32] fp32 copy for the exact rerank (optional)
+//   nbr0   [N][s0]          layer-0 neighbour ids, s0 = Mmax0 rounded up to 4,
+//                           valid ids first, then 0xFFFFFFFF
+//   upoff  [N]              first upper-layer row of an element (0xFFFFFFFF at level 0)
+//   nbrU   [rows][sU]       upper rows; element i's row for layer lc >= 1 is
+//                           upoff[i] + lc - 1; sU = Mmax rounded up to 4
+//   work   [kWorkSlots]     work-queue counters of the persistent search kernel
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "../../include/hnsw.h"
+
+namespace hnswgb {
+
+constexpr int kWorkSlots = 1024;
+constexpr int kMaxEf = 1024;   // ef' limit of the search kernel
+constexpr int kMaxK = 1024;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+struct DevIndex {
+    const uint4* vec;
+    const float* scale;
+    const uint4* vec32;
+    const uint32_t* nbr0;
+    const uint32_t* upoff;
+    const uint32_t* nbrU;
+    uint32_t N, d;
+    uint32_t row_chunks, row_chunks32;
+    uint32_t s0, sU, Mmax0, Mmax;
+    uint32_t ep;
+    int32_t maxlevel;
+    int32_t metric;
+    int32_t storage;
+};
+
+// Parameters of the learned early stop (a small MLP over the search state).
+struct StopModel {
+    const void* weights;  // device fp16 weights, layout fixed by the MLP code
+    float threshold;      // stop when sigmoid(out) > threshold
+    int period;           // evaluate every `period` expansions
+};
+
+}  // namespace hnswgb
+
+struct hnsw_index {
+    hnswgb::DevIndex dev{};
+    hnsw_index_info info{};
+    // owned device allocations
+    void* d_vec = nullptr;
+    void* d_scale = nullptr;
+    void* d_vec32 = nullptr;
+    void* d_nbr0 = nullptr;
+    void* d_upoff = nullptr;
+    void* d_nbrU = nullptr;
+    uint32_t* d_work = nullptr;
+    void* d_stop = nullptr;  // learned-stop weights (fp16), or null
+    std::atomic<uint32_t> work_next{0};
+    // staging for host-memory queries/results, grown on demand
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    int device = 0;
+};

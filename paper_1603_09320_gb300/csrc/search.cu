@@ -1,0 +1,745 @@
+// search.cu -- batched K-NN-SEARCH (arXiv:1603.09320, Alg. 5) on one GPU.
+//
+// One warp answers one query at a time; warps pull query indexes from a
+// device work counter until the batch is exhausted (persistent kernel).
+//
+// Per query:
+//   1. greedy ef=1 descent through layers L..1 (Alg. 5 lines 4-6).  Under key
+//      order (distance, id), SEARCH-LAYER with ef=1 is steepest descent: move
+//      to the best of the current element's neighbours while it beats the
+//      current element.  No visited set is needed for that.
+//   2. SEARCH-LAYER(q, ep, ef', 0) (Alg. 2, ef' = max(ef, K)) as ONE list W in
+//      shared memory, sorted by key and capped at ef', with an "expanded" bit
+//      per entry instead of the two priority queues: under key order the
+//      unextracted candidates that can still be expanded before the break of
+//      lines 7-8 are exactly the unexpanded entries of W, so "extract the
+//      nearest of C" is "take the first unexpanded entry" and the loop ends
+//      when none is left.  All unvisited neighbours of the expanded element
+//      are scored together and merged at once; sequential insertion by lines
+//      12-17 leaves the same top-ef' of the union.
+//   3. the K first entries of W (Alg. 5 line 8), or, with rerank, the K best
+//      of W by exact fp32 distance recomputed from the fp32 copy.
+//
+// Visited set: an open-addressing hash of element ids in shared memory,
+// probed linearly with atomicCAS; when a probe sequence is full the home slot
+// is overwritten, so the set may FORGET an element.  Forgetting never changes
+// the result: an element met again is either already in W (its key equals an
+// entry's key and the merge drops it) or, being outside W after it was
+// visited, has a key above the furthest entry of a full W and is rejected.
+// It only costs a repeated distance evaluation, counted in n_eval.
+//
+// Distances: each row is read as 16-byte chunks by a team of TEAM lanes
+// (consecutive lanes read consecutive chunks, so a team's load of one row is
+// one contiguous segment), U rows per team in flight, partial sums reduced by
+// warp shuffles inside the team.  fp32 accumulation throughout.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "common.hpp"
+#include "index.cuh"
+
+namespace hnswgb {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
+
+struct SearchArgs {
+    DevIndex ix;
+    const float* q;
+    uint32_t n;
+    int k;
+    int efp;
+    int efcap;      // power of two >= efp
+    int hlog;       // log2 visited slots
+    int warp_smem;  // bytes of shared memory per warp
+    int rerank;
+    uint32_t* out_ids;
+    float* out_dists;
+    hnsw_query_stats* stats;
+    uint32_t* work;
+    StopModel stop;
+};
+
+// ---- keys -----------------------------------------------------------------
+// key = ord(dist) << 32 | id << 1 | expanded.  key >> 1 orders (dist, id).
+__device__ __forceinline__ uint32_t f2ord(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+__device__ __forceinline__ uint64_t mkkey(float d, uint32_t id) {
+    return (uint64_t(f2ord(d)) << 32) | (uint64_t(id) << 1);
+}
+__device__ __forceinline__ uint32_t key_id(uint64_t k) { return uint32_t(k >> 1) & 0x7fffffffu; }
+__device__ __forceinline__ float key_dist(uint64_t k) { return ord2f(uint32_t(k >> 32)); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t w = __shfl_xor_sync(kFull, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_row_chunk(const uint4* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// ---- storage decoding -----------------------------------------------------
+template <int ST>
+struct Store;
+template <>
+struct Store<HNSW_F32> {
+    static constexpr int CPC = 4;
+    __device__ static void decode(const uint4& v, float* x) {
+        x[0] = __uint_as_float(v.x); x[1] = __uint_as_float(v.y);
+        x[2] = __uint_as_float(v.z); x[3] = __uint_as_float(v.w);
+    }
+};
+template <>
+struct Store<HNSW_BF16> {
+    static constexpr int CPC = 8;
+    __device__ static void decode(const uint4& v, float* x) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[2 * i] = __uint_as_float(w[i] << 16);
+            x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+};
+template <>
+struct Store<HNSW_F16> {
+    static constexpr int CPC = 8;
+    __device__ static void decode(const uint4& v, float* x) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h;
+            memcpy(&h, &w[i], 4);
+            const float2 f = __half22float2(h);
+            x[2 * i] = f.x;
+            x[2 * i + 1] = f.y;
+        }
+    }
+};
+template <>
+struct Store<HNSW_FP8E4M3> {
+    static constexpr int CPC = 16;
+    __device__ static void decode(const uint4& v, float* x) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const __nv_fp8x2_storage_t pr = __nv_fp8x2_storage_t((w[i] >> (16 * j)) & 0xffffu);
+                const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pr, __NV_E4M3);
+                __half2 h;
+                memcpy(&h, &hr, 4);
+                const float2 f = __half22float2(h);
+                x[4 * i + 2 * j] = f.x;
+                x[4 * i + 2 * j + 1] = f.y;
+            }
+        }
+    }
+};
+
+// ---- batched distance of n rows -------------------------------------------
+template <int ST, int TEAM, int CPL, int U>
+struct Dist {
+    static constexpr int CPC = Store<ST>::CPC;
+    static constexpr int QF = CPL * CPC;  // query coordinates held per lane
+    static constexpr int TEAMS = 32 / TEAM;
+    static constexpr int RPR = TEAMS * U;  // rows per round
+
+    __device__ static void load_q(const float* qp, uint32_t d, float (&qr)[QF], int lane) {
+        const int tl = lane % TEAM;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int ch = tl + c * TEAM;
+#pragma unroll
+            for (int j = 0; j < CPC; ++j) {
+                const uint32_t co = uint32_t(ch * CPC + j);
+                qr[c * CPC + j] = co < d ? qp[co] : 0.0f;
+            }
+        }
+    }
+
+    // out[r] = distance(q, row ids[r]) for r < n
+    __device__ static void run(const DevIndex& ix, const float (&qr)[QF], const uint32_t* ids, int n,
+                               float* out, int lane) {
+        const int team = lane / TEAM, tl = lane % TEAM;
+        const uint32_t C = ix.row_chunks;
+        for (int base = 0; base < n; base += RPR) {
+            uint4 v[U][CPL];
+            float sc[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = base + u * TEAMS + team;
+                const bool live = r < n;
+                const uint32_t id = live ? ids[r] : 0u;
+                const uint4* rowp = ix.vec + uint64_t(id) * C;
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    const uint32_t ch = uint32_t(tl + c * TEAM);
+                    if (live && ch < C)
+                        v[u][c] = ld_row_chunk(rowp + ch);
+                    else
+                        v[u][c] = make_uint4(0u, 0u, 0u, 0u);
+                }
+                if (ST == HNSW_FP8E4M3) sc[u] = live ? __ldg(ix.scale + id) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    float x[CPC];
+                    Store<ST>::decode(v[u][c], x);
+                    if (ix.metric == HNSW_L2SQ) {
+#pragma unroll
+                        for (int j = 0; j < CPC; ++j) {
+                            const float xv = ST == HNSW_FP8E4M3 ? x[j] * sc[u] : x[j];
+                            const float t = qr[c * CPC + j] - xv;
+                            acc = fmaf(t, t, acc);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < CPC; ++j) {
+                            const float xv = ST == HNSW_FP8E4M3 ? x[j] * sc[u] : x[j];
+                            acc = fmaf(qr[c * CPC + j], xv, acc);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = TEAM / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+                const int r = base + u * TEAMS + team;
+                if (tl == 0 && r < n) out[r] = ix.metric == HNSW_L2SQ ? acc : 1.0f - acc;
+            }
+        }
+    }
+};
+
+// exact fp32 distances from the fp32 copy (rerank): teams of 8 lanes, q in smem
+__device__ void dist32_rows(const DevIndex& ix, const float* qs, const uint32_t* ids, int n, float* out, int lane) {
+    const int team = lane >> 3, tl = lane & 7;
+    const uint32_t C = ix.row_chunks32;
+    const float4* q4 = reinterpret_cast<const float4*>(qs);
+    for (int base = 0; base < n; base += 4) {
+        const int r = base + team;
+        const bool live = r < n;
+        const uint4* rowp = ix.vec32 + uint64_t(live ? ids[r] : 0u) * C;
+        float acc = 0.0f;
+        for (uint32_t ch = tl; ch < C; ch += 8) {
+            if (!live) break;
+            const uint4 v = ld_row_chunk(rowp + ch);
+            const float4 qq = q4[ch];
+            const float x[4] = {__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w)};
+            const float qv[4] = {qq.x, qq.y, qq.z, qq.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (ix.metric == HNSW_L2SQ) {
+                    const float t = qv[j] - x[j];
+                    acc = fmaf(t, t, acc);
+                } else {
+                    acc = fmaf(qv[j], x[j], acc);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (tl == 0 && live) out[r] = ix.metric == HNSW_L2SQ ? acc : 1.0f - acc;
+    }
+}
+
+// ---- visited set ------------------------------------------------------------
+// returns true when `id` was not in the set (and records it)
+__device__ __forceinline__ bool visit_new(uint32_t* H, int hlog, uint32_t id, uint32_t& flags) {
+    const uint32_t mask = (1u << hlog) - 1u;
+    const uint32_t h = (id * 2654435761u) >> (32 - hlog);
+#pragma unroll 1
+    for (uint32_t p = 0; p < 16; ++p) {
+        const uint32_t s = (h + p) & mask;
+        const uint32_t old = atomicCAS(&H[s], kNone, id);
+        if (old == kNone) return true;
+        if (old == id) return false;
+    }
+    H[h] = id;  // table region full: forget the home slot's element
+    flags |= 1u;
+    return true;
+}
+
+__device__ __forceinline__ int lower_bound_key(const uint64_t* W, int size, uint64_t k1) {
+    int lo = 0, hi = size;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((W[mid] >> 1) < k1)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Merges the n scored neighbours (ids[], dst[]) into W; returns the smallest
+// index that received a new entry (INT_MAX if none).
+__device__ int merge_batch(uint64_t* W, int& size, int efp, const uint32_t* ids, const float* dst, int n,
+                           uint64_t* ck, uint32_t* lbs, int lane) {
+    const bool full = size >= efp;
+    const uint64_t wlast = size > 0 ? (W[size - 1] >> 1) : 0ull;
+    int m = 0;
+    for (int h = 0; h < n; h += 32) {
+        const int j = h + lane;
+        bool ok = false;
+        uint64_t k = 0;
+        int lb = 0;
+        if (j < n) {
+            k = mkkey(dst[j], ids[j]);
+            ok = !(full && (k >> 1) > wlast);
+            if (ok) {
+                lb = lower_bound_key(W, size, k >> 1);
+                if (lb < size && (W[lb] >> 1) == (k >> 1)) ok = false;  // already in W
+            }
+        }
+        const unsigned msk = __ballot_sync(kFull, ok);
+        if (ok) {
+            const int pos = m + __popc(msk & lanemask_lt());
+            ck[pos] = k;
+            lbs[pos] = uint32_t(lb);
+        }
+        m += __popc(msk);
+    }
+    __syncwarp();
+    if (m == 0) return INT_MAX;
+    // final positions of the new entries: lb + rank among the new entries
+    uint64_t myk[2] = {0ull, 0ull};
+    int mypos[2] = {INT_MAX, INT_MAX};
+    uint32_t mylb = 0xffffffffu;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int j = t * 32 + lane;
+        if (j < m) {
+            const uint64_t k = ck[j];
+            int r = 0;
+            for (int i = 0; i < m; ++i) r += (ck[i] >> 1) < (k >> 1);
+            myk[t] = k;
+            mypos[t] = int(lbs[j]) + r;
+            mylb = min(mylb, lbs[j]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mylb = min(mylb, __shfl_xor_sync(kFull, mylb, o));
+    const int lbmin = int(mylb);
+    // shift the old entries from lbmin up, top chunk first
+    int hi = size;
+    while (hi > lbmin) {
+        const int lo = max(lbmin, hi - 32);
+        const int i = lo + lane;
+        const bool act = i < hi;
+        uint64_t v = 0ull;
+        int cnt = 0;
+        if (act) {
+            v = W[i];
+            for (int j = 0; j < m; ++j) cnt += int(lbs[j]) <= i;
+        }
+        __syncwarp();
+        if (act && i + cnt < efp) W[i + cnt] = v;
+        __syncwarp();
+        hi = lo;
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (mypos[t] < efp) W[mypos[t]] = myk[t];
+    size = min(efp, size + m);
+    __syncwarp();
+    return lbmin;
+}
+
+// warp-wide bitonic sort of n (power of two) keys in shared memory
+__device__ void warp_sort(uint64_t* a, int n, int lane) {
+    for (int kk = 2; kk <= n; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < n; i += 32) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const uint64_t x = a[i], y = a[p];
+                    const bool up = (i & kk) == 0;
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[p] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+}
+
+// ---- the kernel -------------------------------------------------------------
+template <int ST, int TEAM, int CPL, int U>
+__global__ void __launch_bounds__(128) hnsw_search_kernel(const SearchArgs a) {
+    using D = Dist<ST, TEAM, CPL, U>;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    uint8_t* wbase = smem + (threadIdx.x >> 5) * a.warp_smem;
+    uint64_t* W = reinterpret_cast<uint64_t*>(wbase);
+    uint32_t* H = reinterpret_cast<uint32_t*>(wbase + a.efcap * 8);
+    uint32_t* ids = H + (1 << a.hlog);
+    float* dst = reinterpret_cast<float*>(ids + kMaxDeg);
+    uint64_t* ck = reinterpret_cast<uint64_t*>(dst + kMaxDeg);
+    uint32_t* lbs = reinterpret_cast<uint32_t*>(ck + kMaxDeg);
+    float* qs = reinterpret_cast<float*>(lbs + kMaxDeg);
+    const DevIndex& ix = a.ix;
+    const int hsz = 1 << a.hlog;
+
+    for (;;) {
+        uint32_t qi = 0;
+        if (lane == 0) qi = atomicAdd(a.work, 1u);
+        qi = __shfl_sync(kFull, qi, 0);
+        if (qi >= a.n) break;
+        const float* qp = a.q + uint64_t(qi) * ix.d;
+        float qr[D::QF];
+        D::load_q(qp, ix.d, qr, lane);
+        if (a.rerank)
+            for (uint32_t i = lane; i < ix.row_chunks32 * 4; i += 32) qs[i] = i < ix.d ? qp[i] : 0.0f;
+        for (int i = lane; i < hsz; i += 32) H[i] = kNone;
+        uint32_t n_eval = 0, n_exp0 = 0, n_stepU = 0, flags = 0;
+        int size = 0;
+        __syncwarp();
+        if (ix.N > 0) {
+            // enter point and greedy descent (Alg. 5 lines 2-6)
+            if (lane == 0) ids[0] = ix.ep;
+            __syncwarp();
+            D::run(ix, qr, ids, 1, dst, lane);
+            __syncwarp();
+            uint64_t cur = mkkey(dst[0], ix.ep);
+            n_eval = 1;
+            for (int lc = ix.maxlevel; lc >= 1; --lc) {
+                for (;;) {
+                    const uint32_t c = key_id(cur);
+                    const uint64_t row = uint64_t(__ldg(ix.upoff + c)) + uint64_t(lc - 1);
+                    const uint32_t* urow = ix.nbrU + row * ix.sU;
+                    int n = 0;
+                    __syncwarp();
+                    for (int h = 0; h < int(ix.Mmax); h += 32) {
+                        const int j = h + lane;
+                        const uint32_t e = j < int(ix.Mmax) ? __ldg(urow + j) : kNone;
+                        const bool v = e != kNone;
+                        const unsigned m = __ballot_sync(kFull, v);
+                        if (v) ids[n + __popc(m & lanemask_lt())] = e;
+                        n += __popc(m);
+                    }
+                    __syncwarp();
+                    D::run(ix, qr, ids, n, dst, lane);
+                    __syncwarp();
+                    n_eval += n;
+                    uint64_t kb = lane < n ? mkkey(dst[lane], ids[lane]) : ~0ull;
+                    kb = warp_min_u64(kb);
+                    if ((kb >> 1) < (cur >> 1)) {
+                        cur = kb;
+                        ++n_stepU;
+                    } else {
+                        break;
+                    }
+                }
+            }
+            // layer 0 beam (Alg. 2 with ef')
+            if (lane == 0) {
+                W[0] = cur & ~1ull;
+                visit_new(H, a.hlog, key_id(cur), flags);
+            }
+            size = 1;
+            int scan = 0;
+            __syncwarp();
+            for (;;) {
+                int p = -1;
+                for (int s = scan; s < size; s += 32) {
+                    const int i = s + lane;
+                    const bool un = i < size && !(W[i] & 1ull);
+                    const unsigned m = __ballot_sync(kFull, un);
+                    if (m) {
+                        p = s + __ffs(m) - 1;
+                        break;
+                    }
+                }
+                if (p < 0) break;  // every entry of W expanded: lines 7-8
+                const uint64_t kc = W[p];
+                __syncwarp();
+                if (lane == 0) W[p] = kc | 1ull;
+                ++n_exp0;
+                const uint32_t c = key_id(kc);
+                const uint32_t* nrow = ix.nbr0 + uint64_t(c) * ix.s0;
+                int n = 0;
+                for (int h = 0; h < int(ix.Mmax0); h += 32) {
+                    const int j = h + lane;
+                    const uint32_t e = j < int(ix.Mmax0) ? __ldg(nrow + j) : kNone;
+                    const bool nw = e != kNone && visit_new(H, a.hlog, e, flags);
+                    const unsigned m = __ballot_sync(kFull, nw);
+                    if (nw) ids[n + __popc(m & lanemask_lt())] = e;
+                    n += __popc(m);
+                }
+                __syncwarp();
+                int first_new = INT_MAX;
+                if (n > 0) {
+                    D::run(ix, qr, ids, n, dst, lane);
+                    __syncwarp();
+                    n_eval += n;
+                    first_new = merge_batch(W, size, a.efp, ids, dst, n, ck, lbs, lane);
+                }
+                scan = min(p + 1, first_new);
+            }
+        }
+        // results (Alg. 5 line 8)
+        if (a.rerank && size > 0) {
+            for (int b = 0; b < size; b += kMaxDeg) {
+                const int nb = min(kMaxDeg, size - b);
+                for (int i = lane; i < nb; i += 32) ids[i] = key_id(W[b + i]);
+                __syncwarp();
+                dist32_rows(ix, qs, ids, nb, dst, lane);
+                __syncwarp();
+                for (int i = lane; i < nb; i += 32) W[b + i] = mkkey(dst[i], ids[i]);
+                __syncwarp();
+            }
+            for (int i = size + lane; i < a.efcap; i += 32) W[i] = ~0ull;
+            __syncwarp();
+            warp_sort(W, a.efcap, lane);
+        }
+        for (int i = lane; i < a.k; i += 32) {
+            uint32_t oid = kNone;
+            float od = __int_as_float(0x7f800000);
+            if (i < size) {
+                const uint64_t kk = W[i];
+                oid = key_id(kk);
+                od = key_dist(kk);
+            }
+            a.out_ids[uint64_t(qi) * a.k + i] = oid;
+            a.out_dists[uint64_t(qi) * a.k + i] = od;
+        }
+        if (a.stats && lane == 0) {
+            hnsw_query_stats s;
+            s.n_eval = n_eval;
+            s.n_exp0 = n_exp0;
+            s.n_stepU = n_stepU;
+            s.flags = flags;
+            a.stats[qi] = s;
+        }
+        __syncwarp();
+    }
+}
+
+// ---- host side --------------------------------------------------------------
+namespace {
+
+using KernelFn = void (*)(const SearchArgs);
+
+struct KernelChoice {
+    KernelFn fn;
+    const char* name;
+};
+
+template <int ST, int TEAM, int CPL, int U>
+KernelChoice pick() {
+    return {hnsw_search_kernel<ST, TEAM, CPL, U>, "hnsw_search_kernel"};
+}
+
+// (storage, chunks per row) -> instantiation
+bool choose_kernel(int storage, uint32_t chunks, KernelChoice& kc) {
+    switch (storage) {
+        case HNSW_F32:
+            if (chunks <= 2) { kc = pick<HNSW_F32, 2, 1, 2>(); return true; }
+            if (chunks <= 8) { kc = pick<HNSW_F32, 8, 1, 8>(); return true; }
+            if (chunks <= 32) { kc = pick<HNSW_F32, 8, 4, 2>(); return true; }
+            if (chunks <= 128) { kc = pick<HNSW_F32, 32, 4, 1>(); return true; }
+            return false;
+        case HNSW_BF16:
+            if (chunks <= 2) { kc = pick<HNSW_BF16, 2, 1, 2>(); return true; }
+            if (chunks <= 16) { kc = pick<HNSW_BF16, 8, 2, 4>(); return true; }
+            if (chunks <= 64) { kc = pick<HNSW_BF16, 32, 2, 1>(); return true; }
+            return false;
+        case HNSW_F16:
+            if (chunks <= 2) { kc = pick<HNSW_F16, 2, 1, 2>(); return true; }
+            if (chunks <= 16) { kc = pick<HNSW_F16, 8, 2, 4>(); return true; }
+            if (chunks <= 64) { kc = pick<HNSW_F16, 32, 2, 1>(); return true; }
+            return false;
+        case HNSW_FP8E4M3:
+            if (chunks <= 8) { kc = pick<HNSW_FP8E4M3, 8, 1, 8>(); return true; }
+            if (chunks <= 32) { kc = pick<HNSW_FP8E4M3, 32, 1, 1>(); return true; }
+            return false;
+    }
+    return false;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int ceil_log2(uint64_t x) {
+    int r = 0;
+    while ((1ull << r) < x) ++r;
+    return r;
+}
+
+std::mutex g_attr_mu;
+
+}  // namespace
+
+int auto_visited_log2(int efp) {
+    // about 16 slots per beam entry: the evaluations of a layer-0 search are
+    // typically 10-30 x ef'; overflow only costs repeated evaluations
+    int l = ceil_log2(uint64_t(efp) * 16);
+    return l < 10 ? 10 : (l > 13 ? 13 : l);
+}
+
+hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n,
+                          uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
+                          uint32_t* work, const StopModel* stop) {
+    const DevIndex& D = ix->dev;
+    KernelChoice kc;
+    if (!choose_kernel(D.storage, D.row_chunks, kc)) return fail(HNSW_EINVAL, "search: unsupported row size");
+    SearchArgs a{};
+    a.ix = D;
+    a.q = q;
+    a.n = n;
+    a.k = p.k;
+    a.efp = p.ef > p.k ? p.ef : p.k;
+    a.efcap = 1 << ceil_log2(uint64_t(a.efp < 32 ? 32 : a.efp));
+    a.hlog = p.visited_log2 > 0 ? p.visited_log2 : auto_visited_log2(a.efp);
+    a.rerank = p.rerank;
+    a.out_ids = ids;
+    a.out_dists = dists;
+    a.stats = stats;
+    a.work = work;
+    if (stop) a.stop = *stop;
+    const size_t per_warp = size_t(a.efcap) * 8 + (size_t(1) << a.hlog) * 4 + kMaxDeg * (4 + 4 + 8 + 4) +
+                            size_t(D.row_chunks32) * 16;
+    a.warp_smem = int((per_warp + 15) & ~size_t(15));
+    int warps = 4;
+    while (warps > 1 && size_t(warps) * a.warp_smem > 227 * 1024) warps >>= 1;
+    const size_t smem = size_t(warps) * a.warp_smem;
+    if (smem > 227 * 1024) return fail(HNSW_EINVAL, "search: ef/visited set too large for shared memory");
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    {
+        std::lock_guard<std::mutex> lk(g_attr_mu);
+        cudaError_t e = cudaFuncSetAttribute(kc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("search: smem attribute: ") + cudaGetErrorString(e));
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc.fn, warps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t need = (uint64_t(n) + warps - 1) / warps;
+    const uint64_t cap = uint64_t(per_sm) * uint64_t(sms);
+    const unsigned grid = unsigned(need < cap ? need : cap);
+    kc.fn<<<grid, warps * 32, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("search launch: ") + cudaGetErrorString(e));
+    return HNSW_OK;
+}
+
+}  // namespace hnswgb
+
+using namespace hnswgb;
+
+extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* p, const float* queries, int64_t n,
+                                      uint32_t* out_ids, float* out_dists, hnsw_query_stats* stats, void* stream) {
+    if (!ix || !p) return fail(HNSW_EINVAL, "hnsw_search: null index or params");
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(HNSW_EINVAL, "hnsw_search: n out of range");
+    if (p->k < 1 || p->k > kMaxK || p->ef < 1) return fail(HNSW_EINVAL, "hnsw_search: k or ef out of range");
+    if ((p->ef > p->k ? p->ef : p->k) > kMaxEf) return fail(HNSW_EINVAL, "hnsw_search: ef' above 1024");
+    if (p->visited_log2 != 0 && (p->visited_log2 < 5 || p->visited_log2 > 15))
+        return fail(HNSW_EINVAL, "hnsw_search: visited_log2 outside [5,15]");
+    if (p->rerank && !ix->dev.vec32) return fail(HNSW_EINVAL, "hnsw_search: rerank needs the fp32 copy");
+    if (n == 0) return HNSW_OK;
+    if (!queries || !out_ids || !out_dists) return fail(HNSW_EINVAL, "hnsw_search: null buffer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool dq = is_device_ptr(queries), di = is_device_ptr(out_ids), dd = is_device_ptr(out_dists);
+    const bool ds = stats ? is_device_ptr(stats) : true;
+    const size_t qb = size_t(n) * ix->dev.d * 4, ob = size_t(n) * p->k * 4, sb = stats ? size_t(n) * 16 : 0;
+    const float* q = queries;
+    uint32_t* ids = out_ids;
+    float* dists = out_dists;
+    hnsw_query_stats* st = stats;
+    if (!dq || !di || !dd || !ds) {
+        const size_t need = al256(qb) + 2 * al256(ob) + al256(sb);
+        if (ix->stage_bytes < need) {
+            if (ix->stage) {
+                cudaStreamSynchronize(s);
+                cudaFree(ix->stage);
+                ix->stage = nullptr;
+                ix->stage_bytes = 0;
+            }
+            if (cudaMalloc(&ix->stage, need) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(HNSW_ENOMEM, "hnsw_search: staging buffer");
+            }
+            ix->stage_bytes = need;
+        }
+        uint8_t* sp = static_cast<uint8_t*>(ix->stage);
+        if (!dq) {
+            q = reinterpret_cast<const float*>(sp);
+            cudaError_t e = cudaMemcpyAsync(sp, queries, qb, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search: H2D: ") + cudaGetErrorString(e));
+        }
+        sp += al256(qb);
+        if (!di) ids = reinterpret_cast<uint32_t*>(sp);
+        sp += al256(ob);
+        if (!dd) dists = reinterpret_cast<float*>(sp);
+        sp += al256(ob);
+        if (!ds) st = reinterpret_cast<hnsw_query_stats*>(sp);
+    }
+    const uint32_t slot = ix->work_next.fetch_add(1) % kWorkSlots;
+    uint32_t* work = ix->d_work + slot;
+    cudaError_t e = cudaMemsetAsync(work, 0, 4, s);
+    if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search: memset: ") + cudaGetErrorString(e));
+    StopModel sm{};
+    const StopModel* smp = nullptr;
+    hnsw_status r = launch_search(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp);
+    if (r != HNSW_OK) return r;
+    if (!di || !dd || !ds) {
+        if (!di) cudaMemcpyAsync(out_ids, ids, ob, cudaMemcpyDeviceToHost, s);
+        if (!dd) cudaMemcpyAsync(out_dists, dists, ob, cudaMemcpyDeviceToHost, s);
+        if (!ds) cudaMemcpyAsync(stats, st, sb, cudaMemcpyDeviceToHost, s);
+    }
+    if (!dq || !di || !dd || !ds) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search: ") + cudaGetErrorString(e));
+    }
+    (void)sm;
+    return HNSW_OK;
+}
+
+extern "C" hnsw_status hnsw_search(hnsw_index* ix, const float* queries, int64_t n, int32_t k, int32_t ef,
+                                   uint32_t* out_ids, float* out_dists, void* stream) {
+    hnsw_search_params p{};
+    p.k = k;
+    p.ef = ef;
+    p.stop_threshold = 2.0f;
+    return hnsw_search_ex(ix, &p, queries, n, out_ids, out_dists, nullptr, stream);
+}

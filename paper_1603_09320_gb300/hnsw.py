@@ -1,0 +1,202 @@
+"""Thin Python binding of the C ABI in include/hnsw.h (argument marshalling only).
+
+Every step of the search runs in the CUDA kernels of libhnsw_gb300.so; this
+module only converts arguments.  Loading fails loudly when the library has not
+been built (``python -m paper_1603_09320_gb300.build``): there is no fallback.
+Buffers may be numpy arrays (host) or torch tensors (host or CUDA).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NO_ID = 0xFFFFFFFF
+L2SQ, COSINE = 0, 1
+F32, BF16, FP8E4M3, F16 = 0, 1, 2, 3
+DTYPES = {"f32": F32, "bf16": BF16, "fp8": FP8E4M3, "f16": F16}
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECORRUPT", 5: "ETIMEOUT", 6: "EBUSY"}
+
+
+class HnswError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("M", C.c_uint32), ("Mmax", C.c_uint32), ("Mmax0", C.c_uint32),
+                ("ef_construction", C.c_uint32), ("mL", C.c_double), ("heuristic", C.c_int32),
+                ("extend_candidates", C.c_int32), ("keep_pruned", C.c_int32), ("n_threads", C.c_int32)]
+
+
+class IndexInfo(C.Structure):
+    _fields_ = [("N", C.c_uint64), ("d", C.c_uint32), ("d_pad", C.c_uint32), ("row_bytes", C.c_uint32),
+                ("metric", C.c_int32), ("storage", C.c_int32), ("has_fp32", C.c_int32),
+                ("M", C.c_uint32), ("Mmax", C.c_uint32), ("Mmax0", C.c_uint32), ("max_level", C.c_int32),
+                ("enter_point", C.c_uint32), ("n_upper_rows", C.c_uint64), ("device_bytes", C.c_uint64)]
+
+
+class SearchParams(C.Structure):
+    _fields_ = [("k", C.c_int32), ("ef", C.c_int32), ("rerank", C.c_int32), ("visited_log2", C.c_int32),
+                ("stop_threshold", C.c_float), ("stop_period", C.c_int32), ("reserved", C.c_int32 * 2)]
+
+
+class QueryStats(C.Structure):
+    _fields_ = [("n_eval", C.c_uint32), ("n_exp0", C.c_uint32), ("n_stepU", C.c_uint32), ("flags", C.c_uint32)]
+
+
+_lib = None
+EXPORTS = ["hnsw_build", "hnsw_free_blob", "hnsw_upload_index", "hnsw_free_index", "hnsw_get_index_info",
+           "hnsw_search", "hnsw_search_ex", "hnsw_last_error", "hnsw_abi_version"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libhnsw_gb300.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: run python -m paper_1603_09320_gb300.build")
+        L = C.CDLL(path)
+        vp, u32, u64, i32, i64 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.c_int64
+        sig = {
+            "hnsw_build": (i32, [vp, u64, u32, i32, C.POINTER(BuildParams), vp, C.POINTER(vp), C.POINTER(u64)]),
+            "hnsw_free_blob": (None, [vp]),
+            "hnsw_upload_index": (i32, [vp, u64, i32, i32, vp, C.POINTER(vp)]),
+            "hnsw_free_index": (i32, [vp]),
+            "hnsw_get_index_info": (i32, [vp, C.POINTER(IndexInfo)]),
+            "hnsw_search": (i32, [vp, vp, i64, i32, i32, vp, vp, vp]),
+            "hnsw_search_ex": (i32, [vp, C.POINTER(SearchParams), vp, i64, vp, vp, vp, vp]),
+            "hnsw_last_error": (C.c_char_p, []),
+            "hnsw_abi_version": (i32, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int) -> None:
+    if st != 0:
+        raise HnswError(st, lib().hnsw_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """(address, keepalive) of a numpy array or torch tensor."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be C-contiguous")
+        return x.ctypes.data, x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def build_graph(data: np.ndarray, level_u: np.ndarray, metric: int = L2SQ, M: int = 16, Mmax: int | None = None,
+                Mmax0: int | None = None, ef_construction: int = 200, mL: float | None = None,
+                heuristic: bool = True, extend_candidates: bool = False, keep_pruned: bool = False,
+                n_threads: int = 0) -> bytes:
+    """Multi-threaded host construction (Alg. 1 + Alg. 4); returns an HNSWGB01 blob."""
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    u = np.ascontiguousarray(level_u, dtype=np.float64)
+    N, d = data.shape
+    if u.shape != (N,):
+        raise ValueError("level_u must hold one value per element")
+    p = BuildParams(M, M if Mmax is None else Mmax, 2 * M if Mmax0 is None else Mmax0, ef_construction,
+                    1.0 / np.log(M) if mL is None else mL, int(heuristic), int(extend_candidates),
+                    int(keep_pruned), n_threads)
+    out = C.c_void_p()
+    nbytes = C.c_uint64()
+    _check(lib().hnsw_build(data.ctypes.data, N, d, metric, C.byref(p), u.ctypes.data, C.byref(out),
+                            C.byref(nbytes)))
+    try:
+        return C.string_at(out.value, nbytes.value)
+    finally:
+        lib().hnsw_free_blob(out)
+
+
+class Index:
+    """A graph resident on the current CUDA device."""
+
+    def __init__(self, blob: bytes, storage: str | int = "f32", keep_fp32: bool = False, stream=None):
+        st = DTYPES[storage] if isinstance(storage, str) else int(storage)
+        buf = np.frombuffer(blob, dtype=np.uint8)
+        h = C.c_void_p()
+        _check(lib().hnsw_upload_index(buf.ctypes.data, buf.size, st, int(keep_fp32), _stream_ptr(stream),
+                                       C.byref(h)))
+        self.h = h
+        self.info = IndexInfo()
+        _check(lib().hnsw_get_index_info(self.h, C.byref(self.info)))
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().hnsw_free_index(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def d(self) -> int:
+        return int(self.info.d)
+
+    def search_into(self, queries, k: int, ef: int, out_ids, out_dists, stats=None, rerank: bool = False,
+                    visited_log2: int = 0, stream=None) -> None:
+        """hnsw_search_ex into caller-owned buffers (host or device)."""
+        n = int(queries.shape[0]) if queries is not None else 0
+        p = SearchParams(k, ef, int(rerank), visited_log2, 2.0, 0)
+        qp, _a = _ptr(queries)
+        ip, _b = _ptr(out_ids)
+        dp, _c = _ptr(out_dists)
+        sp, _d = _ptr(stats)
+        _check(lib().hnsw_search_ex(self.h, C.byref(p), qp, n, ip, dp, sp, _stream_ptr(stream)))
+
+    def search(self, queries, k: int, ef: int, rerank: bool = False, stats: bool = False, visited_log2: int = 0,
+               stream=None):
+        """Returns (ids, dists[, stats]) as arrays/tensors on the queries' device."""
+        if hasattr(queries, "is_cuda") and queries.is_cuda:
+            import torch
+            n = queries.shape[0]
+            ids = torch.empty((n, k), dtype=torch.int32, device=queries.device)
+            ds = torch.empty((n, k), dtype=torch.float32, device=queries.device)
+            st = torch.empty((n, 4), dtype=torch.int32, device=queries.device) if stats else None
+        else:
+            queries = np.ascontiguousarray(queries, dtype=np.float32)
+            n = queries.shape[0]
+            ids = np.empty((n, k), dtype=np.uint32)
+            ds = np.empty((n, k), dtype=np.float32)
+            st = np.empty((n, 4), dtype=np.uint32) if stats else None
+        self.search_into(queries, k, ef, ids, ds, st, rerank=rerank, visited_log2=visited_log2, stream=stream)
+        return (ids, ds, st) if stats else (ids, ds)

@@ -1,0 +1,174 @@
+"""GPU parity of hnsw_search (Alg. 5) against the oracle on the same graph.
+
+Integer-valued data (tiny, sift-shaped) make every fp32 partial sum exact, so
+ids AND distances must be identical to the oracle's.  Cosine and low-d data
+are compared within the stated tolerance: relative distance error <= 1e-5 and
+result-set overlap >= 0.999.
+"""
+import numpy as np
+import pytest
+
+from paper_1603_09320_gb300 import synth
+from _graphs import oracle_graph, recall
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1603_09320_gb300 import build, hnsw
+    build.build()
+    return hnsw
+
+
+def gpu_search(H, blob, Q, k, ef, storage="f32", keep=False, rerank=False, stats=False, vlog=0, device=True):
+    import torch
+    ix = H.Index(blob, storage, keep_fp32=keep)
+    if device:
+        q = torch.from_numpy(np.ascontiguousarray(Q, dtype=np.float32)).cuda()
+        r = ix.search(q, k, ef, rerank=rerank, stats=stats, visited_log2=vlog)
+        torch.cuda.synchronize()
+        out = [x.cpu().numpy() for x in r]
+        out[0] = out[0].view(np.uint32)
+        if stats:
+            out[2] = out[2].view(np.uint32)
+    else:
+        out = list(ix.search(Q, k, ef, rerank=rerank, stats=stats, visited_log2=vlog))
+    ix.close()
+    return out
+
+
+def oracle_batch(g, Q, k, ef):
+    return g.knn_search_batch(Q, k, ef, stats=True)
+
+
+@pytest.mark.parametrize("k,ef", [(10, 32), (1, 1), (10, 5), (5, 64), (100, 128), (10, 512)])
+def test_tiny_bit_exact(H, k, ef):
+    g, X, blob = oracle_graph("tiny", 10_000)
+    Q = synth.queries("tiny", 1000)
+    gi, gd, gs = gpu_search(H, blob, Q, k, ef, stats=True)
+    oi, od, os_ = oracle_batch(g, Q, k, ef)
+    np.testing.assert_array_equal(gi, oi)
+    np.testing.assert_array_equal(gd.astype(np.float64), od)
+    # the same expansions: layer 0 (n_exp0) and upper rows read (n_stepU)
+    np.testing.assert_array_equal(gs[:, 1], os_[:, 1])
+    np.testing.assert_array_equal(gs[:, 2], os_[:, 2])
+
+
+def test_tiny_host_pointers_and_ragged(H):
+    g, X, blob = oracle_graph("tiny", 10_000)
+    Q = synth.queries("tiny", 77)  # not a multiple of the warps per block
+    gi, gd = gpu_search(H, blob, Q, 10, 32, device=False)
+    oi, od, _ = oracle_batch(g, Q, 10, 32)
+    np.testing.assert_array_equal(gi, oi)
+    np.testing.assert_array_equal(gd.astype(np.float64), od)
+    for n in (1, 31, 33):
+        gi, gd = gpu_search(H, blob, Q[:n], 10, 32)
+        np.testing.assert_array_equal(gi, oi[:n])
+
+
+@pytest.mark.parametrize("vlog", [5, 6, 8])
+def test_lossy_visited_set_same_result(H, vlog):
+    # a tiny visited set forgets elements; results must not change
+    g, X, blob = oracle_graph("tiny", 10_000)
+    Q = synth.queries("tiny", 300)
+    gi, gd, gs = gpu_search(H, blob, Q, 10, 64, stats=True, vlog=vlog)
+    oi, od, os_ = oracle_batch(g, Q, 10, 64)
+    np.testing.assert_array_equal(gi, oi)
+    np.testing.assert_array_equal(gd.astype(np.float64), od)
+    np.testing.assert_array_equal(gs[:, 1], os_[:, 1])
+    assert (gs[:, 3] & 1).any()  # the set did overflow
+
+
+@pytest.mark.parametrize("storage,keep,rerank", [("f32", False, False), ("bf16", False, False),
+                                                 ("bf16", True, True), ("f32", True, True)])
+def test_sift_shaped_bit_exact(H, storage, keep, rerank):
+    # integer coordinates 0..255: bf16 stores them exactly, so bf16 is lossless
+    g, X, blob = oracle_graph("sift", 20_000)
+    Q = synth.queries("sift", 500)
+    gi, gd = gpu_search(H, blob, Q, 10, 64, storage=storage, keep=keep, rerank=rerank)
+    oi, od, _ = oracle_batch(g, Q, 10, 64)
+    np.testing.assert_array_equal(gi, oi)
+    np.testing.assert_array_equal(gd.astype(np.float64), od)
+
+
+def _tolerance_check(gi, gd, oi, od, overlap_min=0.999, rel=1e-5):
+    ov = np.mean([len(set(gi[i]) & set(oi[i])) / gi.shape[1] for i in range(gi.shape[0])])
+    assert ov >= overlap_min, ov
+    m = gi == oi
+    err = np.abs(gd[m].astype(np.float64) - od[m]) / np.maximum(np.abs(od[m]), 1e-30)
+    assert err.max() <= rel, err.max()
+
+
+def test_glove_cosine_tolerance(H):
+    g, X, blob = oracle_graph("glove", 8000)
+    Q = synth.queries("glove", 500)
+    gi, gd = gpu_search(H, blob, Q, 10, 64)
+    oi, od, _ = oracle_batch(g, Q, 10, 64)
+    # cosine distances near 0 make relative error large: compare 1 - d (similarity)
+    _tolerance_check(gi, 1.0 - gd.astype(np.float64), oi, 1.0 - od)
+
+
+def test_lowd_tolerance(H):
+    g, X, blob = oracle_graph("lowd", 20_000)
+    Q = synth.queries("lowd", 500)
+    for k, ef in ((1, 10), (10, 48)):
+        gi, gd = gpu_search(H, blob, Q, k, ef)
+        oi, od, _ = oracle_batch(g, Q, k, ef)
+        _tolerance_check(gi, gd, oi, od)
+
+
+@pytest.mark.parametrize("storage", ["fp8", "f16"])
+def test_quantised_with_rerank(H, storage):
+    # lossy storage: the returned distances are exact fp32 distances of the
+    # returned ids (rerank), and recall stays close to the exact search
+    from oracle import oracle as O
+    name = "sift" if storage == "fp8" else "lowd"
+    g, X, blob = oracle_graph(name, 20_000)
+    Q = synth.queries(name, 300)
+    gi, gd = gpu_search(H, blob, Q, 10, 96, storage=storage, keep=True, rerank=True)
+    for i in range(0, 300, 7):
+        ex = np.array([g.dist(Q[i], int(j)) for j in gi[i]])
+        np.testing.assert_allclose(gd[i], ex, rtol=1e-5, atol=1e-6)
+        assert np.all(np.diff(gd[i]) >= 0)
+    bi, _ = O.brute_force(X, Q, 10)
+    oi, _, _ = oracle_batch(g, Q, 10, 96)
+    assert recall(gi, bi) >= recall(oi, bi) - 0.02
+
+
+def test_padding_when_fewer_than_k(H):
+    from oracle import oracle as O
+    X = synth.base("tiny", 7)
+    g = O.Graph.build(X, synth.level_uniforms("tiny", 7), **synth.params("tiny"))
+    Q = synth.queries("tiny", 5)
+    gi, gd = gpu_search(H, g.to_blob(), Q, 10, 20)
+    oi, od, _ = oracle_batch(g, Q, 10, 20)
+    np.testing.assert_array_equal(gi, oi)
+    assert (gi[:, 7:] == 0xFFFFFFFF).all() and np.isinf(gd[:, 7:]).all()
+
+
+def test_single_element_and_empty_batch(H):
+    from oracle import oracle as O
+    X = synth.base("tiny", 1)
+    g = O.Graph.build(X, np.array([1.0]), **synth.params("tiny"))
+    Q = synth.queries("tiny", 3)
+    gi, gd = gpu_search(H, g.to_blob(), Q, 2, 4)
+    assert (gi[:, 0] == 0).all() and (gi[:, 1] == 0xFFFFFFFF).all()
+    gi, gd = gpu_search(H, g.to_blob(), Q[:0], 2, 4)
+    assert gi.shape == (0, 2)
+
+
+def test_invalid_arguments(H):
+    import torch
+    g, X, blob = oracle_graph("tiny", 10_000)
+    ix = H.Index(blob)
+    q = torch.zeros((4, 32), device="cuda")
+    with pytest.raises(H.HnswError):
+        ix.search(q, 0, 10)
+    with pytest.raises(H.HnswError):
+        ix.search(q, 10, 2000)
+    with pytest.raises(H.HnswError):
+        ix.search(q, 10, 10, rerank=True)  # no fp32 copy kept for f32? kept only with keep_fp32
+    ix.close()
