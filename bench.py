@@ -40,7 +40,7 @@ EF_SWEEP = [10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320,
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-base", type=int, default=1_000_000)
@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--forms", default="f32,bf16r,fp8r")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--profile-once", action="store_true", help="one warm step of the chosen form, then exit")
+    ap.add_argument("--profile-form", default=None,
+                    help="profiling run: upload only this form and launch the search --profile-launches times")
+    ap.add_argument("--profile-ef", type=int, default=64)
+    ap.add_argument("--profile-launches", type=int, default=3)
     return ap.parse_args()
 
 
@@ -129,7 +132,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -318,6 +321,8 @@ def main():
         pg.barrier()
     hnsw.lib()
     X, Q, u = workload(args)
+    if args.profile_form:
+        return profile_run(args, X, Q, u, log)
     build_s = None
     if rank == 0:
         blob, build_s = graph_blob(args, X, u, log)
@@ -339,10 +344,6 @@ def main():
     cands = [n for n in ok if n != "f32"] or ["f32"]
     chosen = min(cands, key=lambda n: timing[n])
     fc = ok[chosen]
-    if args.profile_once:
-        indexes[chosen].search_into(bufs[0], args.k, fc["ef"], bufs[1], bufs[2], bufs[3], rerank=fc["rerank"])
-        torch.cuda.synchronize()
-        return
     # ---- timed region ----------------------------------------------------
     clocks = Clocks(local, enabled=not args.no_clocks and rank == 0)
     if pg:
@@ -418,6 +419,27 @@ def main():
     out["cpu_baseline"]["recall_at_10"] = cpu["recall"]
     out["cpu_baseline"]["oracle_n_dist_mean"] = cpu["n_dist_mean"]
     print(json.dumps(out), flush=True)
+
+
+def profile_run(args, X, Q, u, log):
+    """Uploads one form and launches the search a few times (for ncu)."""
+    import torch
+    from paper_1603_09320_gb300 import hnsw
+    blob, _ = graph_blob(args, X, u, log)
+    storage, keep, rerank = FORMS[args.profile_form]
+    ix = hnsw.Index(blob, storage, keep_fp32=keep)
+    q = torch.from_numpy(Q).cuda()
+    n, k = Q.shape[0], args.k
+    ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    ds = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    st = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    for _ in range(args.profile_launches):
+        ix.search_into(q, k, args.profile_ef, ids, ds, st, rerank=rerank)
+    torch.cuda.synchronize()
+    s = st.cpu().numpy().view(np.uint32)
+    ab, cnt = algorithmic_bytes(ix.info, s, k, args.profile_ef, rerank, X.shape[1])
+    print(json.dumps({"profile_form": args.profile_form, "ef": args.profile_ef, "launches": args.profile_launches,
+                      "algorithmic_bytes_per_launch": ab, "counters": cnt}), flush=True)
 
 
 def reference_arm(args, rank, world, log):

@@ -452,11 +452,11 @@ __global__ void __launch_bounds__(128) hnsw_search_kernel(const SearchArgs a) {
                     D::run(ix, qr, ids, n, dst, lane);
                     __syncwarp();
                     n_eval += n;
+                    ++n_stepU;  // one upper-layer element expanded (its row read)
                     uint64_t kb = lane < n ? mkkey(dst[lane], ids[lane]) : ~0ull;
                     kb = warp_min_u64(kb);
                     if ((kb >> 1) < (cur >> 1)) {
                         cur = kb;
-                        ++n_stepU;
                     } else {
                         break;
                     }
