@@ -177,6 +177,25 @@ hnsw_status hnsw_search_ex(hnsw_index* index, const hnsw_search_params* params,
                            const float* queries, int64_t n, uint32_t* out_ids, float* out_dists,
                            hnsw_query_stats* stats, void* stream);
 
+/* hnsw_search without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc while
+ * searching -- a process whose device memory is all reserved by another
+ * allocator (e.g. a framework's caching allocator), or a latency-critical
+ * path that must avoid cudaMalloc/cudaFree, which synchronise the device.
+ * Same arguments and results as hnsw_search (ef' = max(ef, k)).  Host-memory
+ * buffers are staged through one fixed 16 MiB device array that the library
+ * holds on every GPU it is loaded on until exit; a batch whose host buffers
+ * need more than that (queries n*d*4 bytes, ids and distances n*k*4 bytes
+ * each, 256-byte aligned, plus 256 bytes for the kernel's work counter) is
+ * rejected with HNSW_EINVAL -- pass device buffers or split the batch.  The
+ * first call on each device looks up that array's address (make it before
+ * any stream capture).  All calls share the array: calls whose GPU work
+ * overlaps race, so issue them one after another.  The index must have been
+ * uploaded (which allocates) beforehand, on the current device.
+ * Errors: as hnsw_search, plus HNSW_EINVAL for the size limit. */
+hnsw_status hnsw_search_noalloc(hnsw_index* index, const float* queries, int64_t n, int32_t k, int32_t ef,
+                                uint32_t* out_ids, float* out_dists, void* stream);
+
 /* Thread-local message describing the last failure of this thread. */
 const char* hnsw_last_error(void);
 
