@@ -20,9 +20,9 @@
 //   3. the K first entries of W (Alg. 5 line 8), or, with rerank, the K best
 //      of W by exact fp32 distance recomputed from the fp32 copy.
 //
-// Visited set: an open-addressing hash of element ids in shared memory,
-// probed linearly with atomicCAS; when a probe sequence is full the home slot
-// is overwritten, so the set may FORGET an element.  Forgetting never changes
+// Visited set: a 4-way bucketed hash of element ids in shared memory; when a
+// bucket is full one of its slots is overwritten, so the set may FORGET an
+// element.  Forgetting never changes
 // the result: an element met again is either already in W (its key equals an
 // entry's key and the merge drops it) or, being outside W after it was
 // visited, has a key above the furthest entry of a full W and is rejected.
@@ -49,6 +49,37 @@ namespace hnswgb {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
+
+// Tuning switches (compile time).  HNSW_PREFETCH_ROWS: after the visited
+// check, every lane owning a new neighbour prefetches its whole row into L2,
+// so the later gather rounds of the batch hit L2 instead of waiting on DRAM
+// one after another.  HNSW_PREFETCH_NEXT: while an element is expanded, the
+// neighbour row of the next unexpanded entry of W is loaded speculatively;
+// it is the next element to expand unless the current batch inserts a better
+// one.  HNSW_MIN_BLOCKS: minimum resident blocks per SM for the register
+// allocation of the search kernel (0: let ptxas choose).
+#ifndef HNSW_PREFETCH_ROWS
+#define HNSW_PREFETCH_ROWS 0
+#endif
+#ifndef HNSW_PREFETCH_NEXT
+#define HNSW_PREFETCH_NEXT 1
+#endif
+#ifndef HNSW_MIN_BLOCKS
+#define HNSW_MIN_BLOCKS 0
+#endif
+// rows gathered per team and round for fp32 rows of 128 coordinates and for
+// bf16/f16 rows of up to 128 coordinates
+#ifndef HNSW_F32_U
+#define HNSW_F32_U 2
+#endif
+#ifndef HNSW_B16_U
+#define HNSW_B16_U 2
+#endif
+#if HNSW_MIN_BLOCKS > 0
+#define HNSW_SEARCH_BOUNDS __launch_bounds__(128, HNSW_MIN_BLOCKS)
+#else
+#define HNSW_SEARCH_BOUNDS __launch_bounds__(128)
+#endif
 
 struct SearchArgs {
     DevIndex ix;
@@ -89,13 +120,23 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t w = __shfl_xor_sync(kFull, v, o);
-        v = w < v ? w : v;
-    }
-    return v;
+    const uint32_t hi = uint32_t(v >> 32), lo = uint32_t(v);
+    const uint32_t mh = __reduce_min_sync(kFull, hi);
+    const uint32_t ml = __reduce_min_sync(kFull, hi == mh ? lo : 0xffffffffu);
+    return (uint64_t(mh) << 32) | ml;
 }
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// 16-byte asynchronous global -> shared copy (no registers held while in flight)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ uint4 ld_row_chunk(const uint4* p) {
     uint4 v;
@@ -165,7 +206,8 @@ struct Store<HNSW_FP8E4M3> {
 };
 
 // ---- batched distance of n rows -------------------------------------------
-template <int ST, int TEAM, int CPL, int U>
+// FULL: every row has exactly TEAM * CPL chunks (no per-chunk bounds test)
+template <int ST, int TEAM, int CPL, int U, bool FULL>
 struct Dist {
     static constexpr int CPC = Store<ST>::CPC;
     static constexpr int QF = CPL * CPC;  // query coordinates held per lane
@@ -202,7 +244,7 @@ struct Dist {
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
                     const uint32_t ch = uint32_t(tl + c * TEAM);
-                    if (live && ch < C)
+                    if (live && (FULL || ch < C))
                         v[u][c] = ld_row_chunk(rowp + ch);
                     else
                         v[u][c] = make_uint4(0u, 0u, 0u, 0u);
@@ -273,19 +315,24 @@ __device__ void dist32_rows(const DevIndex& ix, const float* qs, const uint32_t*
 }
 
 // ---- visited set ------------------------------------------------------------
-// returns true when `id` was not in the set (and records it)
+// 4-way bucketed hash of element ids: one 16-byte shared load reads a whole
+// bucket; a miss stores the id into the bucket's first empty slot, or, when
+// the bucket is full, over slot (id & 3) -- the set then forgets that slot's
+// element (harmless, see the file header).  Two lanes of a warp inserting
+// into the same slot at once lose one of the ids the same way.
+// Returns true when `id` was not in the set (and records it).
 __device__ __forceinline__ bool visit_new(uint32_t* H, int hlog, uint32_t id, uint32_t& flags) {
-    const uint32_t mask = (1u << hlog) - 1u;
-    const uint32_t h = (id * 2654435761u) >> (32 - hlog);
-#pragma unroll 1
-    for (uint32_t p = 0; p < 16; ++p) {
-        const uint32_t s = (h + p) & mask;
-        const uint32_t old = atomicCAS(&H[s], kNone, id);
-        if (old == kNone) return true;
-        if (old == id) return false;
+    const uint32_t b = (id * 2654435761u) >> (34 - hlog);  // bucket index, 2^(hlog-2) buckets
+    uint4* bp = reinterpret_cast<uint4*>(H) + b;
+    const uint4 v = *bp;
+    if (v.x == id || v.y == id || v.z == id || v.w == id) return false;
+    uint32_t* sl = reinterpret_cast<uint32_t*>(bp);
+    int slot = v.x == kNone ? 0 : (v.y == kNone ? 1 : (v.z == kNone ? 2 : (v.w == kNone ? 3 : -1)));
+    if (slot < 0) {
+        slot = int(id & 3u);
+        flags |= 1u;
     }
-    H[h] = id;  // table region full: forget the home slot's element
-    flags |= 1u;
+    sl[slot] = id;
     return true;
 }
 
@@ -331,6 +378,24 @@ __device__ int merge_batch(uint64_t* W, int& size, int efp, const uint32_t* ids,
     }
     __syncwarp();
     if (m == 0) return INT_MAX;
+    if (m == 1) {  // one new entry (the common case once W is full): shift and insert
+        const int lb = int(lbs[0]);
+        const uint64_t k = ck[0];
+        int hi = min(size, efp - 1);
+        while (hi > lb) {
+            const int lo = max(lb, hi - 32);
+            const int i = lo + lane;
+            const uint64_t v = i < hi ? W[i] : 0ull;
+            __syncwarp();
+            if (i < hi) W[i + 1] = v;
+            __syncwarp();
+            hi = lo;
+        }
+        if (lane == 0) W[lb] = k;
+        size = min(efp, size + 1);
+        __syncwarp();
+        return lb;
+    }
     // final positions of the new entries: lb + rank among the new entries
     uint64_t myk[2] = {0ull, 0ull};
     int mypos[2] = {INT_MAX, INT_MAX};
@@ -347,9 +412,7 @@ __device__ int merge_batch(uint64_t* W, int& size, int efp, const uint32_t* ids,
             mylb = min(mylb, lbs[j]);
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mylb = min(mylb, __shfl_xor_sync(kFull, mylb, o));
-    const int lbmin = int(mylb);
+    const int lbmin = int(__reduce_min_sync(kFull, mylb));
     // shift the old entries from lbmin up, top chunk first
     int hi = size;
     while (hi > lbmin) {
@@ -394,10 +457,12 @@ __device__ void warp_sort(uint64_t* a, int n, int lane) {
         }
 }
 
+__device__ __forceinline__ uint32_t ix_row32(const SearchArgs& a) { return a.ix.row_chunks32 * 4; }
+
 // ---- the kernel -------------------------------------------------------------
-template <int ST, int TEAM, int CPL, int U>
-__global__ void __launch_bounds__(128) hnsw_search_kernel(const SearchArgs a) {
-    using D = Dist<ST, TEAM, CPL, U>;
+template <int ST, int TEAM, int CPL, int U, bool FULL>
+__global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
+    using D = Dist<ST, TEAM, CPL, U, FULL>;
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     uint8_t* wbase = smem + (threadIdx.x >> 5) * a.warp_smem;
@@ -408,6 +473,7 @@ __global__ void __launch_bounds__(128) hnsw_search_kernel(const SearchArgs a) {
     uint64_t* ck = reinterpret_cast<uint64_t*>(dst + kMaxDeg);
     uint32_t* lbs = reinterpret_cast<uint32_t*>(ck + kMaxDeg);
     float* qs = reinterpret_cast<float*>(lbs + kMaxDeg);
+    uint32_t* nbuf = reinterpret_cast<uint32_t*>(qs + ix_row32(a));  // staged neighbour row (16-byte aligned)
     const DevIndex& ix = a.ix;
     const int hsz = 1 << a.hlog;
 
@@ -421,7 +487,8 @@ __global__ void __launch_bounds__(128) hnsw_search_kernel(const SearchArgs a) {
         D::load_q(qp, ix.d, qr, lane);
         if (a.rerank)
             for (uint32_t i = lane; i < ix.row_chunks32 * 4; i += 32) qs[i] = i < ix.d ? qp[i] : 0.0f;
-        for (int i = lane; i < hsz; i += 32) H[i] = kNone;
+        for (int i = lane; i < (hsz >> 2); i += 32)
+            reinterpret_cast<uint4*>(H)[i] = make_uint4(kNone, kNone, kNone, kNone);
         uint32_t n_eval = 0, n_exp0 = 0, n_stepU = 0, flags = 0;
         int size = 0;
         __syncwarp();
@@ -469,6 +536,8 @@ __global__ void __launch_bounds__(128) hnsw_search_kernel(const SearchArgs a) {
             }
             size = 1;
             int scan = 0;
+            const int deg = int(ix.Mmax0);
+            uint32_t nxt_id = kNone;  // element whose neighbour row is staged in nbuf
             __syncwarp();
             for (;;) {
                 int p = -1;
@@ -481,25 +550,74 @@ __global__ void __launch_bounds__(128) hnsw_search_kernel(const SearchArgs a) {
                         break;
                     }
                 }
-                if (p < 0) break;  // every entry of W expanded: lines 7-8
+                if (p < 0) {  // every entry of W expanded: lines 7-8
+                    if (nxt_id != kNone) cp_async_wait_all();
+                    break;
+                }
                 const uint64_t kc = W[p];
                 __syncwarp();
                 if (lane == 0) W[p] = kc | 1ull;
                 ++n_exp0;
                 const uint32_t c = key_id(kc);
                 const uint32_t* nrow = ix.nbr0 + uint64_t(c) * ix.s0;
+                // was this row staged in shared memory during the previous expansion?
+                const bool staged = c == nxt_id;
+                if (nxt_id != kNone) {
+                    cp_async_wait_all();
+                    __syncwarp();
+                }
+                uint32_t e0 = kNone, e1 = kNone;
+                if (staged) {
+                    e0 = lane < deg ? nbuf[lane] : kNone;
+                    if (deg > 32) e1 = lane + 32 < deg ? nbuf[32 + lane] : kNone;
+                } else {
+                    e0 = lane < deg ? __ldg(nrow + lane) : kNone;
+                    if (deg > 32) e1 = lane + 32 < deg ? __ldg(nrow + 32 + lane) : kNone;
+                }
+                __syncwarp();
+#if HNSW_PREFETCH_NEXT
+                // the next unexpanded entry after p is expanded next unless this
+                // batch inserts a better element: stage its neighbour row now
+                nxt_id = kNone;
+                {
+                    const int i = p + 1 + lane;
+                    const bool un = i < size && !(W[i] & 1ull);
+                    const unsigned m = __ballot_sync(kFull, un);
+                    if (m) {
+                        const int src = __ffs(m) - 1;
+                        nxt_id = __shfl_sync(kFull, un ? key_id(W[i]) : 0u, src);
+                        const uint32_t* np = ix.nbr0 + uint64_t(nxt_id) * ix.s0;
+                        if (lane * 4 < deg) cp_async16(nbuf + lane * 4, np + lane * 4);
+                        cp_async_commit();
+                    }
+                }
+#endif
                 int n = 0;
-                for (int h = 0; h < int(ix.Mmax0); h += 32) {
-                    const int j = h + lane;
-                    const uint32_t e = j < int(ix.Mmax0) ? __ldg(nrow + j) : kNone;
-                    const bool nw = e != kNone && visit_new(H, a.hlog, e, flags);
+                {
+                    const bool nw = e0 != kNone && visit_new(H, a.hlog, e0, flags);
                     const unsigned m = __ballot_sync(kFull, nw);
-                    if (nw) ids[n + __popc(m & lanemask_lt())] = e;
+                    if (nw) ids[__popc(m & lanemask_lt())] = e0;
+                    n = __popc(m);
+                }
+                if (deg > 32) {
+                    const bool nw = e1 != kNone && visit_new(H, a.hlog, e1, flags);
+                    const unsigned m = __ballot_sync(kFull, nw);
+                    if (nw) ids[n + __popc(m & lanemask_lt())] = e1;
                     n += __popc(m);
                 }
                 __syncwarp();
                 int first_new = INT_MAX;
                 if (n > 0) {
+#if HNSW_PREFETCH_ROWS
+                    // rows beyond the first gather round: start their DRAM reads now
+                    if (n > D::RPR) {
+                        for (int j = D::RPR + lane; j < n; j += 32) {
+                            const uint8_t* rp =
+                                reinterpret_cast<const uint8_t*>(ix.vec + uint64_t(ids[j]) * ix.row_chunks);
+                            for (uint32_t b = 0; b < ix.row_chunks * 16; b += 128) prefetch_l2(rp + b);
+                        }
+                    }
+#endif
                     D::run(ix, qr, ids, n, dst, lane);
                     __syncwarp();
                     n_eval += n;
@@ -557,32 +675,33 @@ struct KernelChoice {
 };
 
 template <int ST, int TEAM, int CPL, int U>
-KernelChoice pick() {
-    return {hnsw_search_kernel<ST, TEAM, CPL, U>, "hnsw_search_kernel"};
+KernelChoice pick(uint32_t chunks) {
+    if (chunks == uint32_t(TEAM * CPL)) return {hnsw_search_kernel<ST, TEAM, CPL, U, true>, "hnsw_search_kernel"};
+    return {hnsw_search_kernel<ST, TEAM, CPL, U, false>, "hnsw_search_kernel"};
 }
 
 // (storage, chunks per row) -> instantiation
 bool choose_kernel(int storage, uint32_t chunks, KernelChoice& kc) {
     switch (storage) {
         case HNSW_F32:
-            if (chunks <= 2) { kc = pick<HNSW_F32, 2, 1, 2>(); return true; }
-            if (chunks <= 8) { kc = pick<HNSW_F32, 8, 1, 8>(); return true; }
-            if (chunks <= 32) { kc = pick<HNSW_F32, 8, 4, 2>(); return true; }
-            if (chunks <= 128) { kc = pick<HNSW_F32, 32, 4, 1>(); return true; }
+            if (chunks <= 2) { kc = pick<HNSW_F32, 2, 1, 2>(chunks); return true; }
+            if (chunks <= 8) { kc = pick<HNSW_F32, 8, 1, 8>(chunks); return true; }
+            if (chunks <= 32) { kc = pick<HNSW_F32, 8, 4, HNSW_F32_U>(chunks); return true; }
+            if (chunks <= 128) { kc = pick<HNSW_F32, 32, 4, 1>(chunks); return true; }
             return false;
         case HNSW_BF16:
-            if (chunks <= 2) { kc = pick<HNSW_BF16, 2, 1, 2>(); return true; }
-            if (chunks <= 16) { kc = pick<HNSW_BF16, 8, 2, 4>(); return true; }
-            if (chunks <= 64) { kc = pick<HNSW_BF16, 32, 2, 1>(); return true; }
+            if (chunks <= 2) { kc = pick<HNSW_BF16, 2, 1, 2>(chunks); return true; }
+            if (chunks <= 16) { kc = pick<HNSW_BF16, 8, 2, HNSW_B16_U>(chunks); return true; }
+            if (chunks <= 64) { kc = pick<HNSW_BF16, 32, 2, 1>(chunks); return true; }
             return false;
         case HNSW_F16:
-            if (chunks <= 2) { kc = pick<HNSW_F16, 2, 1, 2>(); return true; }
-            if (chunks <= 16) { kc = pick<HNSW_F16, 8, 2, 4>(); return true; }
-            if (chunks <= 64) { kc = pick<HNSW_F16, 32, 2, 1>(); return true; }
+            if (chunks <= 2) { kc = pick<HNSW_F16, 2, 1, 2>(chunks); return true; }
+            if (chunks <= 16) { kc = pick<HNSW_F16, 8, 2, 4>(chunks); return true; }
+            if (chunks <= 64) { kc = pick<HNSW_F16, 32, 2, 1>(chunks); return true; }
             return false;
         case HNSW_FP8E4M3:
-            if (chunks <= 8) { kc = pick<HNSW_FP8E4M3, 8, 1, 8>(); return true; }
-            if (chunks <= 32) { kc = pick<HNSW_FP8E4M3, 32, 1, 1>(); return true; }
+            if (chunks <= 8) { kc = pick<HNSW_FP8E4M3, 8, 1, 8>(chunks); return true; }
+            if (chunks <= 32) { kc = pick<HNSW_FP8E4M3, 32, 1, 1>(chunks); return true; }
             return false;
     }
     return false;
@@ -638,7 +757,7 @@ hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const flo
     a.work = work;
     if (stop) a.stop = *stop;
     const size_t per_warp = size_t(a.efcap) * 8 + (size_t(1) << a.hlog) * 4 + kMaxDeg * (4 + 4 + 8 + 4) +
-                            size_t(D.row_chunks32) * 16;
+                            size_t(D.row_chunks32) * 16 + kMaxDeg * 4;
     a.warp_smem = int((per_warp + 15) & ~size_t(15));
     int warps = 4;
     while (warps > 1 && size_t(warps) * a.warp_smem > 227 * 1024) warps >>= 1;
