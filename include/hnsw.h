@@ -166,8 +166,11 @@ typedef struct {
     int32_t rerank;          /* 1: recompute fp32 distances of all ef' final candidates
                                 from the fp32 copy and return the top k of those */
     int32_t visited_log2;    /* log2 of visited-set slots per query, 0 = automatic */
-    float stop_threshold;    /* learned stop: stop when sigmoid(MLP) > threshold; >= 1 disables */
-    int32_t stop_period;     /* learned stop: evaluate every stop_period expansions */
+    float stop_threshold;    /* learned stop: in (0,1) stop the layer-0 beam when the stop
+                                network's sigmoid exceeds it (needs hnsw_set_stop_model);
+                                <= 0 or >= 1: off, the plain search */
+    int32_t stop_period;     /* learned stop / trace: check every stop_period layer-0
+                                expansions (<= 0: 4) */
     int32_t reserved[2];
 } hnsw_search_params;
 
@@ -176,6 +179,62 @@ typedef struct {
 hnsw_status hnsw_search_ex(hnsw_index* index, const hnsw_search_params* params,
                            const float* queries, int64_t n, uint32_t* out_ids, float* out_dists,
                            hnsw_query_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned early stop of the layer-0 beam (an addition: the paper has none)  */
+/* ------------------------------------------------------------------------ */
+/* A network 6 -> 64 -> 64 -> 1 (ReLU, fp16 weights, fp32 arithmetic) reads
+ * the search state every stop_period layer-0 expansions and predicts whether
+ * the current top-k of W is already final.  Features (d1 = distance of the
+ * element where the upper-layer descent ended, clamped below by 1e-12):
+ * log1p(best/d1), log1p(worst/d1), log1p(layer-0 distance evaluations),
+ * log1p(d1), log1p(expansions since the k-th best entry last improved),
+ * log1p(kth/d1), where best/worst/kth are distances of W's entries.
+ * Weights: 4,673 fp16 values in the order W1 (64x6, row-major out x in), b1,
+ * W2 (64x64), b2, w3 (64), b3; normalisation: mean[6] then std[6], applied as
+ * (x - mean) / std before the first layer. */
+#define HNSW_STOP_NPARAM 4673
+
+/* Installs (or replaces) the index's stop network; host arrays. */
+hnsw_status hnsw_set_stop_model(hnsw_index* index, const float* norm12, const uint16_t* w_fp16);
+hnsw_status hnsw_clear_stop_model(hnsw_index* index);
+
+/* Runs the search of hnsw_search_ex without stopping early and records, at
+ * every check (every stop_period layer-0 expansions once W holds k entries),
+ * the six features into feats[n][max_checks][6], the ids of W's current top
+ * k into topk[n][max_checks][k] and, when logits is not NULL and the index
+ * has a stop network, its logit into logits[n][max_checks]; n_checks[n]
+ * receives the number of checks recorded (at most max_checks).  All buffers
+ * are device memory; asynchronous on stream. */
+hnsw_status hnsw_search_trace(hnsw_index* index, const hnsw_search_params* params, const float* queries,
+                              int64_t n, int32_t max_checks, float* feats, uint32_t* topk, float* logits,
+                              int32_t* n_checks, uint32_t* out_ids, float* out_dists,
+                              hnsw_query_stats* stats, void* stream);
+
+/* Gradient of the mean binary cross-entropy of the network over n samples
+ * (x: device [n][6] raw features, y: device [n] labels in {0,1}) at the given
+ * fp16 weights and normalisation (host); writes grad_out[4673] and the mean
+ * loss (host).  Synchronous. */
+hnsw_status hnsw_stop_grad(const float* x, const float* y, int64_t n, const float* norm12,
+                           const uint16_t* w_fp16, float* grad_out, float* loss_out, void* stream);
+
+typedef struct {
+    int32_t epochs;       /* passes over the samples */
+    int32_t batch;        /* samples per optimiser step, a multiple of 128 */
+    float lr;             /* Adam step size */
+    float beta1, beta2, eps;  /* Adam constants (0: 0.9, 0.999, 1e-8) */
+    float weight_decay;   /* L2 coefficient added to the gradient */
+    uint64_t seed;        /* sample visiting order */
+} hnsw_stop_train_params;
+
+/* Trains the network on the GPU from w_init (host fp16): normalisation from
+ * the samples' mean and std, then epochs of Adam on fp32 master weights with
+ * fp16 working weights.  Writes norm_out[12], w_out[4673] (host) and, when
+ * not NULL, the mean loss of every epoch.  x, y: device memory as in
+ * hnsw_stop_grad.  Synchronous. */
+hnsw_status hnsw_stop_train(const float* x, const float* y, int64_t n, const hnsw_stop_train_params* params,
+                            const uint16_t* w_init, float* norm_out, uint16_t* w_out, float* loss_per_epoch,
+                            void* stream);
 
 /* hnsw_search without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc while

@@ -182,10 +182,21 @@ int orc_level_from_u(double u, double mL) { return (int)floor(-log(u) * mL); }
 /* Alg. 2  SEARCH-LAYER(q, ep, ef, lc)                                       */
 /* ------------------------------------------------------------------------ */
 
+/* Optional recording of the search state on layer 0 (for the learned-stop
+ * features): after every T-th expansion, once |W| >= K, the nearest,
+ * furthest and K-th nearest distances of W, the layer-0 distance evaluations
+ * so far, the enter point's distance d1, the expansions since the K-th
+ * nearest last improved, and the ids of the K nearest. */
+typedef struct {
+    int K, T, max_checks, n_checks;
+    double* raw;      /* [max_checks][6]: best, worst, kth, n_eval0, d1, stale */
+    uint32_t* topk;   /* [max_checks][K] */
+} orc_trace;
+
 /* ep given as items (id with its distance to q already known).  Result W is
  * written sorted ascending by key; returns |W|, or -1 on allocation failure. */
-static int search_layer_items(const orc_graph* g, const float* q, const orc_item* ep, int n_ep,
-                              int ef, int lc, orc_item* out, orc_stats* st) {
+static int search_layer_items_tr(const orc_graph* g, const float* q, const orc_item* ep, int n_ep,
+                                 int ef, int lc, orc_item* out, orc_stats* st, orc_trace* tr) {
     unsigned char* v = (unsigned char*)calloc(g->N > 0 ? g->N : 1, 1);
     orc_heap C, W;
     if (!v || !heap_init(&C, 64, 0) || !heap_init(&W, ef + 2, 1)) { free(v); return -1; }
@@ -196,6 +207,9 @@ static int search_layer_items(const orc_graph* g, const float* q, const orc_item
         heap_push(&C, ep[i]);
         heap_push(&W, ep[i]);
     }
+    uint64_t n_eval0 = 0, n_exp = 0, stale = 0;
+    orc_item last_kth = { INFINITY, ORC_NONE };
+    orc_item* sorted = tr ? (orc_item*)malloc(sizeof(orc_item) * (size_t)(ef + n_ep + 2)) : NULL;
     /* line 4 */
     while (C.n > 0) {
         orc_item c = heap_pop(&C);              /* line 5: nearest in C */
@@ -210,13 +224,40 @@ static int search_layer_items(const orc_graph* g, const float* q, const orc_item
             f = W.a[0];                         /* line 12 */
             orc_item ei = { dist_vec(g, q, row(g, e)), e };
             if (st) st->n_dist++;
+            n_eval0++;
             if (key_less(ei, f) || W.n < ef) {  /* line 13 */
                 heap_push(&C, ei);              /* line 14 */
                 heap_push(&W, ei);              /* line 15 */
                 if (W.n > ef) heap_pop(&W);     /* lines 16-17 */
             }
         }
+        if (tr && sorted) {   /* state after this expansion */
+            n_exp++;
+            int nw = W.n;
+            for (int i = 0; i < nw; ++i) sorted[i] = W.a[i];
+            qsort(sorted, (size_t)nw, sizeof(orc_item), cmp_item);
+            if (nw >= tr->K && key_less(sorted[tr->K - 1], last_kth)) {
+                last_kth = sorted[tr->K - 1];
+                stale = 0;
+            } else {
+                stale++;
+            }
+            if (nw >= tr->K && n_exp % (uint64_t)tr->T == 0) {
+                if (tr->n_checks < tr->max_checks) {
+                    double* r = tr->raw + 6 * (size_t)tr->n_checks;
+                    r[0] = sorted[0].d;
+                    r[1] = sorted[nw - 1].d;
+                    r[2] = sorted[tr->K - 1].d;
+                    r[3] = (double)n_eval0;
+                    r[4] = ep[0].d;
+                    r[5] = (double)stale;
+                    for (int i = 0; i < tr->K; ++i) tr->topk[(size_t)tr->n_checks * tr->K + i] = sorted[i].id;
+                }
+                tr->n_checks++;
+            }
+        }
     }
+    free(sorted);
     int n = W.n;
     for (int i = 0; i < n; ++i) out[i] = W.a[i];
     qsort(out, (size_t)n, sizeof(orc_item), cmp_item);
@@ -224,6 +265,11 @@ static int search_layer_items(const orc_graph* g, const float* q, const orc_item
     heap_free(&W);
     free(v);
     return n;
+}
+
+static int search_layer_items(const orc_graph* g, const float* q, const orc_item* ep, int n_ep,
+                              int ef, int lc, orc_item* out, orc_stats* st) {
+    return search_layer_items_tr(g, q, ep, n_ep, ef, lc, out, st, NULL);
 }
 
 int orc_search_layer(const orc_graph* g, const float* q, const uint32_t* ep, int n_ep,
@@ -469,6 +515,26 @@ int orc_knn_search(const orc_graph* g, const float* q, int K, int ef,
     }
     int n = search_layer_items(g, q, &ep, 1, efp, 0, W, st);   /* line 7 */
     for (int i = 0; i < n && i < K; ++i) { ids[i] = W[i].id; dists[i] = W[i].d; }  /* line 8 */
+    free(W);
+    return 0;
+}
+
+int orc_knn_search_trace(const orc_graph* g, const float* q, int K, int ef, int T, int max_checks,
+                         double* raw, uint32_t* topk, int* n_checks) {
+    if (K < 1 || ef < 1 || T < 1 || max_checks < 1) return -1;
+    *n_checks = 0;
+    if (g->n_inserted == 0) return 0;
+    int efp = ef > K ? ef : K;
+    orc_item* W = (orc_item*)malloc(sizeof(orc_item) * (size_t)(efp + 2));
+    if (!W) return -1;
+    orc_item ep = { dist_vec(g, q, row(g, g->ep)), g->ep };
+    for (int lc = g->maxlevel; lc >= 1; --lc) {
+        search_layer_items(g, q, &ep, 1, 1, lc, W, NULL);
+        ep = W[0];
+    }
+    orc_trace tr = { K, T, max_checks, 0, raw, topk };
+    search_layer_items_tr(g, q, &ep, 1, efp, 0, W, NULL, &tr);
+    *n_checks = tr.n_checks < max_checks ? tr.n_checks : max_checks;
     free(W);
     return 0;
 }

@@ -92,6 +92,15 @@ int orc_build(orc_graph* g, const double* u);
 int orc_knn_search(const orc_graph* g, const float* q, int K, int ef,
                    uint32_t* ids, double* dists, orc_stats* st);
 
+/* Alg. 5 recording the layer-0 search state after every T-th expansion once
+ * |W| >= K (up to max_checks records): raw[c][6] = nearest, furthest and K-th
+ * nearest distance of W, layer-0 distance evaluations so far, the layer-0
+ * enter point's distance, expansions since the K-th nearest last improved;
+ * topk[c][K] = ids of the K nearest.  Used to check the learned-stop
+ * features; the search itself is unchanged. */
+int orc_knn_search_trace(const orc_graph* g, const float* q, int K, int ef, int T, int max_checks,
+                         double* raw, uint32_t* topk, int* n_checks);
+
 /* Alg. 2 on layer lc from enter points ep[0..n_ep); returns |W| and writes W
  * sorted ascending by key into out_ids/out_dists (capacity >= ef). */
 int orc_search_layer(const orc_graph* g, const float* q, const uint32_t* ep, int n_ep,

@@ -70,6 +70,7 @@ def lib():
                 "orc_save_blob": (i32, [vp, vp, u64]),
                 "orc_load_blob": (vp, [vp, u64, vp]),
                 "orc_brute_force": (None, [vp, u64, u32, i32, vp, i32, vp, vp]),
+                "orc_knn_search_trace": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -201,6 +202,16 @@ class Graph:
             ids[i], ds[i] = r[0], r[1]
             sts[i] = (r[2].n_dist, r[2].n_hops0, r[2].n_hopsU)
         return (ids, ds, sts) if stats else (ids, ds)
+
+    def knn_search_trace(self, q, K: int, ef: int, T: int = 4, max_checks: int = 256):
+        """Layer-0 state records (see orc_knn_search_trace): (raw[c][6], topk[c][K])."""
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        raw = np.zeros((max_checks, 6), dtype=np.float64)
+        topk = np.zeros((max_checks, K), dtype=np.uint32)
+        nc = C.c_int(0)
+        if lib().orc_knn_search_trace(self.h, _p(q), K, ef, T, max_checks, _p(raw), _p(topk), C.byref(nc)) != 0:
+            raise RuntimeError("orc_knn_search_trace failed")
+        return raw[:nc.value], topk[:nc.value]
 
     def search_layer(self, q, ep, ef: int, lc: int):
         q = np.ascontiguousarray(q, dtype=np.float32)

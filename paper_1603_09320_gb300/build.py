@@ -24,8 +24,8 @@ CU_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-rel
             "-I", INCLUDE]
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE]
 
-SOURCES = ["search.cu", "search_noalloc.cu", "index.cu", "builder.cpp", "blob.cpp"]
-HEADERS = ["common.hpp", "index.cuh"]
+SOURCES = ["search.cu", "search_noalloc.cu", "index.cu", "stopnet.cu", "builder.cpp", "blob.cpp"]
+HEADERS = ["common.hpp", "index.cuh", "stopnet.cuh"]
 
 
 def _obj(src: str) -> str:

@@ -44,11 +44,17 @@ struct DevIndex {
     int32_t storage;
 };
 
-// Parameters of the learned early stop (a small MLP over the search state).
+// Optional parts of one search launch: the learned early stop and the trace
+// recording used to train it (all null/zero: the plain search).
 struct StopModel {
-    const void* weights;  // device fp16 weights, layout fixed by the MLP code
-    float threshold;      // stop when sigmoid(out) > threshold
-    int period;           // evaluate every `period` expansions
+    const void* stop;       // device StopDev, or null
+    float logit_threshold;  // stop when the network's logit exceeds this
+    int period;             // check every `period` layer-0 expansions
+    float* tr_feat;         // trace buffers (device), tr_count == null: no trace
+    uint32_t* tr_topk;
+    float* tr_logit;
+    int32_t* tr_count;
+    int tr_max;
 };
 
 }  // namespace hnswgb

@@ -21,8 +21,9 @@
 //      of W by exact fp32 distance recomputed from the fp32 copy.
 //
 // Visited set: a 4-way bucketed hash of element ids in shared memory; when a
-// bucket is full one of its slots is overwritten, so the set may FORGET an
-// element.  Forgetting never changes
+// bucket is full one of its slots is overwritten, and two lanes storing into
+// the same free slot at the same instant keep only one id, so the set may
+// FORGET an element.  Forgetting never changes
 // the result: an element met again is either already in W (its key equals an
 // entry's key and the merge drops it) or, being outside W after it was
 // visited, has a key above the furthest entry of a full W and is rejected.
@@ -44,6 +45,7 @@
 
 #include "common.hpp"
 #include "index.cuh"
+#include "stopnet.cuh"
 
 namespace hnswgb {
 
@@ -95,7 +97,17 @@ struct SearchArgs {
     float* out_dists;
     hnsw_query_stats* stats;
     uint32_t* work;
-    StopModel stop;
+    // learned stop: model (null: none), decision threshold on the logit,
+    // check period in layer-0 expansions (0: no checks)
+    const StopDev* stop;
+    float stop_logit;
+    int stop_period;
+    // trace mode (tr_count != null): record every check, never stop early
+    float* tr_feat;      // [n][tr_max][6]
+    uint32_t* tr_topk;   // [n][tr_max][k]
+    float* tr_logit;     // [n][tr_max] (only with a model)
+    int32_t* tr_count;   // [n] checks recorded
+    int tr_max;
 };
 
 // ---- keys -----------------------------------------------------------------
@@ -460,7 +472,9 @@ __device__ void warp_sort(uint64_t* a, int n, int lane) {
 __device__ __forceinline__ uint32_t ix_row32(const SearchArgs& a) { return a.ix.row_chunks32 * 4; }
 
 // ---- the kernel -------------------------------------------------------------
-template <int ST, int TEAM, int CPL, int U, bool FULL>
+// STOP: the build with learned-stop checks and trace recording (the plain
+// search is compiled without them and keeps its smaller register budget).
+template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP>
 __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
     using D = Dist<ST, TEAM, CPL, U, FULL>;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -490,6 +504,7 @@ __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
         for (int i = lane; i < (hsz >> 2); i += 32)
             reinterpret_cast<uint4*>(H)[i] = make_uint4(kNone, kNone, kNone, kNone);
         uint32_t n_eval = 0, n_exp0 = 0, n_stepU = 0, flags = 0;
+        int n_checks = 0;
         int size = 0;
         __syncwarp();
         if (ix.N > 0) {
@@ -537,6 +552,9 @@ __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
             size = 1;
             int scan = 0;
             const int deg = int(ix.Mmax0);
+            const float d1 = key_dist(cur);  // where the upper-layer descent ended
+            uint64_t last_kth = ~0ull;        // (dist, id) of the K-th best entry so far
+            uint32_t stale = 0, n_eval0 = 0;
             uint32_t nxt_id = kNone;  // element whose neighbour row is staged in nbuf
             __syncwarp();
             for (;;) {
@@ -621,9 +639,48 @@ __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
                     D::run(ix, qr, ids, n, dst, lane);
                     __syncwarp();
                     n_eval += n;
+                    n_eval0 += n;
                     first_new = merge_batch(W, size, a.efp, ids, dst, n, ck, lbs, lane);
                 }
                 scan = min(p + 1, first_new);
+                if (STOP && a.stop_period > 0) {
+                    // the top-K of W changes exactly when its K-th key decreases
+                    const uint64_t kthk = size >= a.k ? (W[a.k - 1] >> 1) : ~0ull;
+                    if (kthk < last_kth) {
+                        last_kth = kthk;
+                        stale = 0;
+                    } else {
+                        ++stale;
+                    }
+                    if (size >= a.k && n_exp0 % uint32_t(a.stop_period) == 0) {
+                        const float d1n = fmaxf(d1, 1e-12f);
+                        float f[kStopIn];
+                        f[0] = log1pf(fmaxf(key_dist(W[0]) / d1n, 0.0f));
+                        f[1] = log1pf(fmaxf(key_dist(W[size - 1]) / d1n, 0.0f));
+                        f[2] = log1pf(float(n_eval0));
+                        f[3] = log1pf(fmaxf(d1, 0.0f));
+                        f[4] = log1pf(float(stale));
+                        f[5] = log1pf(fmaxf(key_dist(W[a.k - 1]) / d1n, 0.0f));
+                        const float logit = a.stop ? stop_logit(a.stop, f, lane) : 0.0f;
+                        if (a.tr_count) {
+                            if (n_checks < a.tr_max) {
+                                const uint64_t slot = uint64_t(qi) * uint64_t(a.tr_max) + uint64_t(n_checks);
+                                float fv = f[0];
+#pragma unroll
+                                for (int i = 1; i < kStopIn; ++i) fv = lane == i ? f[i] : fv;
+                                if (lane < kStopIn) a.tr_feat[slot * kStopIn + lane] = fv;
+                                if (lane == 0 && a.tr_logit) a.tr_logit[slot] = logit;
+                                for (int i = lane; i < a.k; i += 32) a.tr_topk[slot * uint64_t(a.k) + i] = key_id(W[i]);
+                            }
+                            ++n_checks;
+                        } else if (a.stop && logit > a.stop_logit) {
+                            flags |= 2u;  // learned stop: W's top-K is predicted final
+                            if (nxt_id != kNone) cp_async_wait_all();
+                            __syncwarp();
+                            break;
+                        }
+                    }
+                }
             }
         }
         // results (Alg. 5 line 8)
@@ -652,6 +709,7 @@ __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
             a.out_ids[uint64_t(qi) * a.k + i] = oid;
             a.out_dists[uint64_t(qi) * a.k + i] = od;
         }
+        if (STOP && a.tr_count && lane == 0) a.tr_count[qi] = n_checks < a.tr_max ? n_checks : a.tr_max;
         if (a.stats && lane == 0) {
             hnsw_query_stats s;
             s.n_eval = n_eval;
@@ -675,33 +733,36 @@ struct KernelChoice {
 };
 
 template <int ST, int TEAM, int CPL, int U>
-KernelChoice pick(uint32_t chunks) {
-    if (chunks == uint32_t(TEAM * CPL)) return {hnsw_search_kernel<ST, TEAM, CPL, U, true>, "hnsw_search_kernel"};
-    return {hnsw_search_kernel<ST, TEAM, CPL, U, false>, "hnsw_search_kernel"};
+KernelChoice pick(uint32_t chunks, bool stop) {
+    if (chunks == uint32_t(TEAM * CPL))
+        return {stop ? hnsw_search_kernel<ST, TEAM, CPL, U, true, true> : hnsw_search_kernel<ST, TEAM, CPL, U, true, false>,
+                "hnsw_search_kernel"};
+    return {stop ? hnsw_search_kernel<ST, TEAM, CPL, U, false, true> : hnsw_search_kernel<ST, TEAM, CPL, U, false, false>,
+            "hnsw_search_kernel"};
 }
 
 // (storage, chunks per row) -> instantiation
-bool choose_kernel(int storage, uint32_t chunks, KernelChoice& kc) {
+bool choose_kernel(int storage, uint32_t chunks, bool stop, KernelChoice& kc) {
     switch (storage) {
         case HNSW_F32:
-            if (chunks <= 2) { kc = pick<HNSW_F32, 2, 1, 2>(chunks); return true; }
-            if (chunks <= 8) { kc = pick<HNSW_F32, 8, 1, 8>(chunks); return true; }
-            if (chunks <= 32) { kc = pick<HNSW_F32, 8, 4, HNSW_F32_U>(chunks); return true; }
-            if (chunks <= 128) { kc = pick<HNSW_F32, 32, 4, 1>(chunks); return true; }
+            if (chunks <= 2) { kc = pick<HNSW_F32, 2, 1, 2>(chunks, stop); return true; }
+            if (chunks <= 8) { kc = pick<HNSW_F32, 8, 1, 8>(chunks, stop); return true; }
+            if (chunks <= 32) { kc = pick<HNSW_F32, 8, 4, HNSW_F32_U>(chunks, stop); return true; }
+            if (chunks <= 128) { kc = pick<HNSW_F32, 32, 4, 1>(chunks, stop); return true; }
             return false;
         case HNSW_BF16:
-            if (chunks <= 2) { kc = pick<HNSW_BF16, 2, 1, 2>(chunks); return true; }
-            if (chunks <= 16) { kc = pick<HNSW_BF16, 8, 2, HNSW_B16_U>(chunks); return true; }
-            if (chunks <= 64) { kc = pick<HNSW_BF16, 32, 2, 1>(chunks); return true; }
+            if (chunks <= 2) { kc = pick<HNSW_BF16, 2, 1, 2>(chunks, stop); return true; }
+            if (chunks <= 16) { kc = pick<HNSW_BF16, 8, 2, HNSW_B16_U>(chunks, stop); return true; }
+            if (chunks <= 64) { kc = pick<HNSW_BF16, 32, 2, 1>(chunks, stop); return true; }
             return false;
         case HNSW_F16:
-            if (chunks <= 2) { kc = pick<HNSW_F16, 2, 1, 2>(chunks); return true; }
-            if (chunks <= 16) { kc = pick<HNSW_F16, 8, 2, 4>(chunks); return true; }
-            if (chunks <= 64) { kc = pick<HNSW_F16, 32, 2, 1>(chunks); return true; }
+            if (chunks <= 2) { kc = pick<HNSW_F16, 2, 1, 2>(chunks, stop); return true; }
+            if (chunks <= 16) { kc = pick<HNSW_F16, 8, 2, 4>(chunks, stop); return true; }
+            if (chunks <= 64) { kc = pick<HNSW_F16, 32, 2, 1>(chunks, stop); return true; }
             return false;
         case HNSW_FP8E4M3:
-            if (chunks <= 8) { kc = pick<HNSW_FP8E4M3, 8, 1, 8>(chunks); return true; }
-            if (chunks <= 32) { kc = pick<HNSW_FP8E4M3, 32, 1, 1>(chunks); return true; }
+            if (chunks <= 8) { kc = pick<HNSW_FP8E4M3, 8, 1, 8>(chunks, stop); return true; }
+            if (chunks <= 32) { kc = pick<HNSW_FP8E4M3, 32, 1, 1>(chunks, stop); return true; }
             return false;
     }
     return false;
@@ -741,7 +802,8 @@ hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const flo
                           uint32_t* work, const StopModel* stop) {
     const DevIndex& D = ix->dev;
     KernelChoice kc;
-    if (!choose_kernel(D.storage, D.row_chunks, kc)) return fail(HNSW_EINVAL, "search: unsupported row size");
+    if (!choose_kernel(D.storage, D.row_chunks, stop != nullptr && stop->period > 0, kc))
+        return fail(HNSW_EINVAL, "search: unsupported row size");
     SearchArgs a{};
     a.ix = D;
     a.q = q;
@@ -755,7 +817,16 @@ hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const flo
     a.out_dists = dists;
     a.stats = stats;
     a.work = work;
-    if (stop) a.stop = *stop;
+    if (stop) {
+        a.stop = static_cast<const StopDev*>(stop->stop);
+        a.stop_logit = stop->logit_threshold;
+        a.stop_period = stop->period;
+        a.tr_feat = stop->tr_feat;
+        a.tr_topk = stop->tr_topk;
+        a.tr_logit = stop->tr_logit;
+        a.tr_count = stop->tr_count;
+        a.tr_max = stop->tr_max;
+    }
     const size_t per_warp = size_t(a.efcap) * 8 + (size_t(1) << a.hlog) * 4 + kMaxDeg * (4 + 4 + 8 + 4) +
                             size_t(D.row_chunks32) * 16 + kMaxDeg * 4;
     a.warp_smem = int((per_warp + 15) & ~size_t(15));
@@ -839,6 +910,13 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search: memset: ") + cudaGetErrorString(e));
     StopModel sm{};
     const StopModel* smp = nullptr;
+    if (p->stop_threshold > 0.0f && p->stop_threshold < 1.0f) {
+        if (!ix->d_stop) return fail(HNSW_EINVAL, "hnsw_search: stop_threshold in (0,1) needs a stop model");
+        sm.stop = ix->d_stop;
+        sm.logit_threshold = logf(p->stop_threshold / (1.0f - p->stop_threshold));
+        sm.period = p->stop_period > 0 ? p->stop_period : 4;
+        smp = &sm;
+    }
     hnsw_status r = launch_search(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp);
     if (r != HNSW_OK) return r;
     if (!di || !dd || !ds) {
@@ -850,7 +928,6 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search: ") + cudaGetErrorString(e));
     }
-    (void)sm;
     return HNSW_OK;
 }
 
@@ -861,4 +938,37 @@ extern "C" hnsw_status hnsw_search(hnsw_index* ix, const float* queries, int64_t
     p.ef = ef;
     p.stop_threshold = 2.0f;
     return hnsw_search_ex(ix, &p, queries, n, out_ids, out_dists, nullptr, stream);
+}
+
+extern "C" hnsw_status hnsw_search_trace(hnsw_index* ix, const hnsw_search_params* p, const float* queries,
+                                         int64_t n, int32_t max_checks, float* feats, uint32_t* topk,
+                                         float* logits, int32_t* n_checks, uint32_t* out_ids, float* out_dists,
+                                         hnsw_query_stats* stats, void* stream) {
+    if (!ix || !p) return fail(HNSW_EINVAL, "hnsw_search_trace: null index or params");
+    if (n < 0 || n >= (int64_t(1) << 31) || max_checks < 1) return fail(HNSW_EINVAL, "hnsw_search_trace: n or max_checks");
+    if (p->k < 1 || p->k > kMaxK || p->ef < 1 || (p->ef > p->k ? p->ef : p->k) > kMaxEf)
+        return fail(HNSW_EINVAL, "hnsw_search_trace: k or ef out of range");
+    if (p->rerank && !ix->dev.vec32) return fail(HNSW_EINVAL, "hnsw_search_trace: rerank needs the fp32 copy");
+    if (n == 0) return HNSW_OK;
+    const void* ptrs[] = {queries, feats, topk, n_checks, out_ids, out_dists};
+    for (const void* q : ptrs)
+        if (!is_device_ptr(q)) return fail(HNSW_EINVAL, "hnsw_search_trace: buffers must be device memory");
+    if ((logits && !is_device_ptr(logits)) || (stats && !is_device_ptr(stats)))
+        return fail(HNSW_EINVAL, "hnsw_search_trace: buffers must be device memory");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StopModel sm{};
+    sm.stop = logits ? ix->d_stop : nullptr;
+    sm.logit_threshold = 0.0f;
+    sm.period = p->stop_period > 0 ? p->stop_period : 4;
+    sm.tr_feat = feats;
+    sm.tr_topk = topk;
+    sm.tr_logit = ix->d_stop ? logits : nullptr;
+    sm.tr_count = n_checks;
+    sm.tr_max = max_checks;
+    const uint32_t slot = ix->work_next.fetch_add(1) % kWorkSlots;
+    uint32_t* work = ix->d_work + slot;
+    cudaError_t e = cudaMemsetAsync(work, 0, 4, s);
+    if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search_trace: memset: ") + cudaGetErrorString(e));
+    hnsw_search_params q = *p;
+    return launch_search(ix, q, queries, uint32_t(n), out_ids, out_dists, stats, s, work, &sm);
 }

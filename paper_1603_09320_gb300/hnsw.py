@@ -46,13 +46,17 @@ class SearchParams(C.Structure):
                 ("stop_threshold", C.c_float), ("stop_period", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
+class StopTrainParams(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("weight_decay", C.c_float), ("seed", C.c_uint64)]
+
+
 class QueryStats(C.Structure):
     _fields_ = [("n_eval", C.c_uint32), ("n_exp0", C.c_uint32), ("n_stepU", C.c_uint32), ("flags", C.c_uint32)]
 
 
 _lib = None
-EXPORTS = ["hnsw_build", "hnsw_free_blob", "hnsw_upload_index", "hnsw_free_index", "hnsw_get_index_info",
-           "hnsw_search", "hnsw_search_ex", "hnsw_last_error", "hnsw_abi_version"]
+STOP_NPARAM = 4673
 
 
 def lib_path() -> str:
@@ -77,6 +81,11 @@ def lib():
             "hnsw_search": (i32, [vp, vp, i64, i32, i32, vp, vp, vp]),
             "hnsw_search_ex": (i32, [vp, C.POINTER(SearchParams), vp, i64, vp, vp, vp, vp]),
             "hnsw_last_error": (C.c_char_p, []),
+            "hnsw_set_stop_model": (i32, [vp, vp, vp]),
+            "hnsw_clear_stop_model": (i32, [vp]),
+            "hnsw_search_trace": (i32, [vp, C.POINTER(SearchParams), vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "hnsw_stop_grad": (i32, [vp, vp, i64, vp, vp, vp, vp, vp]),
+            "hnsw_stop_train": (i32, [vp, vp, i64, C.POINTER(StopTrainParams), vp, vp, vp, vp, vp]),
             "hnsw_abi_version": (i32, []),
         }
         for name, (res, args) in sig.items():
@@ -172,11 +181,43 @@ class Index:
     def d(self) -> int:
         return int(self.info.d)
 
+    def set_stop_model(self, norm12, w_fp16) -> None:
+        """Installs the learned-stop network (norm: mean[6], std[6]; 4,673 fp16 weights)."""
+        norm = np.ascontiguousarray(norm12, dtype=np.float32)
+        w = np.ascontiguousarray(w_fp16, dtype=np.float16).view(np.uint16)
+        if norm.size != 12 or w.size != STOP_NPARAM:
+            raise ValueError("norm needs 12 values, weights 4673")
+        _check(lib().hnsw_set_stop_model(self.h, norm.ctypes.data, w.ctypes.data))
+
+    def clear_stop_model(self) -> None:
+        _check(lib().hnsw_clear_stop_model(self.h))
+
+    def search_trace(self, queries, k: int, ef: int, max_checks: int, period: int = 4, logits: bool = False,
+                     rerank: bool = False, visited_log2: int = 0, stream=None):
+        """hnsw_search_trace on CUDA tensors; returns (feats, topk, logits|None,
+        n_checks, ids, dists, stats) as CUDA tensors."""
+        import torch
+        n = queries.shape[0]
+        dev = queries.device
+        feats = torch.zeros((n, max_checks, 6), dtype=torch.float32, device=dev)
+        topk = torch.zeros((n, max_checks, k), dtype=torch.int32, device=dev)
+        lg = torch.zeros((n, max_checks), dtype=torch.float32, device=dev) if logits else None
+        cnt = torch.zeros((n,), dtype=torch.int32, device=dev)
+        ids = torch.empty((n, k), dtype=torch.int32, device=dev)
+        ds = torch.empty((n, k), dtype=torch.float32, device=dev)
+        st = torch.empty((n, 4), dtype=torch.int32, device=dev)
+        p = SearchParams(k, ef, int(rerank), visited_log2, 2.0, period)
+        _check(lib().hnsw_search_trace(self.h, C.byref(p), queries.data_ptr(), n, max_checks, feats.data_ptr(),
+                                       topk.data_ptr(), lg.data_ptr() if lg is not None else None, cnt.data_ptr(),
+                                       ids.data_ptr(), ds.data_ptr(), st.data_ptr(), _stream_ptr(stream)))
+        return feats, topk, lg, cnt, ids, ds, st
+
     def search_into(self, queries, k: int, ef: int, out_ids, out_dists, stats=None, rerank: bool = False,
-                    visited_log2: int = 0, stream=None) -> None:
+                    visited_log2: int = 0, stop_threshold: float = 2.0, stop_period: int = 0,
+                    stream=None) -> None:
         """hnsw_search_ex into caller-owned buffers (host or device)."""
         n = int(queries.shape[0]) if queries is not None else 0
-        p = SearchParams(k, ef, int(rerank), visited_log2, 2.0, 0)
+        p = SearchParams(k, ef, int(rerank), visited_log2, stop_threshold, stop_period)
         qp, _a = _ptr(queries)
         ip, _b = _ptr(out_ids)
         dp, _c = _ptr(out_dists)
@@ -184,7 +225,7 @@ class Index:
         _check(lib().hnsw_search_ex(self.h, C.byref(p), qp, n, ip, dp, sp, _stream_ptr(stream)))
 
     def search(self, queries, k: int, ef: int, rerank: bool = False, stats: bool = False, visited_log2: int = 0,
-               stream=None):
+               stop_threshold: float = 2.0, stop_period: int = 0, stream=None):
         """Returns (ids, dists[, stats]) as arrays/tensors on the queries' device."""
         if hasattr(queries, "is_cuda") and queries.is_cuda:
             import torch
@@ -198,5 +239,30 @@ class Index:
             ids = np.empty((n, k), dtype=np.uint32)
             ds = np.empty((n, k), dtype=np.float32)
             st = np.empty((n, 4), dtype=np.uint32) if stats else None
-        self.search_into(queries, k, ef, ids, ds, st, rerank=rerank, visited_log2=visited_log2, stream=stream)
+        self.search_into(queries, k, ef, ids, ds, st, rerank=rerank, visited_log2=visited_log2,
+                         stop_threshold=stop_threshold, stop_period=stop_period, stream=stream)
         return (ids, ds, st) if stats else (ids, ds)
+
+
+def stop_grad(x, y, norm12, w_fp16):
+    """hnsw_stop_grad: x [n,6] and y [n] CUDA float tensors; returns (grad[4673], loss)."""
+    norm = np.ascontiguousarray(norm12, dtype=np.float32)
+    w = np.ascontiguousarray(w_fp16, dtype=np.float16).view(np.uint16)
+    g = np.zeros(STOP_NPARAM, dtype=np.float32)
+    loss = C.c_float(0)
+    _check(lib().hnsw_stop_grad(x.data_ptr(), y.data_ptr(), x.shape[0], norm.ctypes.data, w.ctypes.data,
+                                g.ctypes.data, C.addressof(loss), _stream_ptr(None)))
+    return g, float(loss.value)
+
+
+def stop_train(x, y, w_init, epochs: int = 20, batch: int = 4096, lr: float = 2e-3, weight_decay: float = 0.0,
+               seed: int = 0):
+    """hnsw_stop_train on CUDA tensors x [n,6], y [n]; returns (norm12, w_fp16, loss_per_epoch)."""
+    w0 = np.ascontiguousarray(w_init, dtype=np.float16).view(np.uint16)
+    norm = np.zeros(12, dtype=np.float32)
+    w = np.zeros(STOP_NPARAM, dtype=np.uint16)
+    ls = np.zeros(epochs, dtype=np.float32)
+    p = StopTrainParams(epochs, batch, lr, 0.0, 0.0, 0.0, weight_decay, seed)
+    _check(lib().hnsw_stop_train(x.data_ptr(), y.data_ptr(), x.shape[0], C.byref(p), w0.ctypes.data,
+                                 norm.ctypes.data, w.ctypes.data, ls.ctypes.data, _stream_ptr(None)))
+    return norm, w.view(np.float16), ls
