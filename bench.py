@@ -48,7 +48,13 @@ def parse():
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--target-recall", type=float, default=0.95)
     ap.add_argument("--threads", type=int, default=0, help="builder threads (0: all)")
-    ap.add_argument("--forms", default="f32,bf16r,fp8r")
+    ap.add_argument("--forms", default="f32,bf16r,fp8r,bf16r_stop")
+    ap.add_argument("--train-queries", type=int, default=20_000, help="learned stop: training queries")
+    ap.add_argument("--stop-efs", type=lambda v: [int(x) for x in v.split(",")], default=[64, 80, 96])
+    ap.add_argument("--stop-thresholds", type=lambda v: [float(x) for x in v.split(",")],
+                    default=[0.5, 0.7, 0.8, 0.85, 0.9, 0.95, 0.98])
+    ap.add_argument("--stop-period", type=int, default=8)
+    ap.add_argument("--stop-epochs", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--profile-form", default=None,
@@ -110,10 +116,11 @@ def recall_at(ids, gt):
 # --------------------------------------------------------------------------
 # GPU side
 # --------------------------------------------------------------------------
-FORMS = {  # name: (storage, keep fp32, rerank)
-    "f32": ("f32", False, False),
-    "bf16r": ("bf16", True, True),
-    "fp8r": ("fp8", True, True),
+FORMS = {  # name: (storage, keep fp32, rerank, learned stop)
+    "f32": ("f32", False, False, False),
+    "bf16r": ("bf16", True, True, False),
+    "fp8r": ("fp8", True, True, False),
+    "bf16r_stop": ("bf16", True, True, True),
 }
 
 
@@ -164,7 +171,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_forms(args, blob, Q, gt, log):
+def run_forms(args, blob, X, Q, gt, log):
     import torch
     from paper_1603_09320_gb300 import hnsw
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -173,43 +180,101 @@ def run_forms(args, blob, Q, gt, log):
     ids = torch.empty((n, k), dtype=torch.int32, device=dev)
     ds = torch.empty((n, k), dtype=torch.float32, device=dev)
     st = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    bufs = (q, ids, ds, st)
     res = {}
     indexes = {}
     for name in args.forms.split(","):
-        storage, keep, rerank = FORMS[name]
+        storage, keep, rerank, stop = FORMS[name]
         ix = hnsw.Index(blob, storage, keep_fp32=keep)
         indexes[name] = ix
+        if stop:
+            res[name] = stop_form(args, ix, X, bufs, gt, rerank, log)
+            continue
         sweep = []
-        chosen = None
+        setting = None
         for ef in EF_SWEEP:
             if ef < k:
                 continue
-            ix.search_into(q, k, ef, ids, ds, st, rerank=rerank)
+            cand = {"ef": ef, "rerank": rerank}
+            _search(ix, args, bufs, cand)
             torch.cuda.synchronize()
             r = recall_at(ids.cpu().numpy().view(np.uint32), gt)
             sweep.append((ef, r))
             if r >= args.target_recall:
-                chosen = ef
+                setting = cand
+                setting["recall"] = r
                 break
-        res[name] = {"storage": storage, "rerank": rerank, "sweep": sweep, "ef": chosen}
+        res[name] = {"storage": storage, "rerank": rerank, "sweep": sweep, "setting": setting}
         log(f"form {name}: sweep {sweep}")
-    return res, indexes, (q, ids, ds, st)
+    return res, indexes, bufs
 
 
-def time_form(args, ix, ef, rerank, bufs, steps, warmup, flush):
+def stop_form(args, ix, X, bufs, gt, rerank, log):
+    """Learned early stop on top of the given index: traces of separate
+    training queries at ef_max, labels against their exact k-NN, training on
+    the GPU, then the (ef_max, threshold) pair with the best time among those
+    reaching the recall target."""
+    import torch
+    from paper_1603_09320_gb300 import stopnet, synth
+    k = args.k
+    Qt = synth.queries("sift", args.train_queries, training=True)
+    gt_t = ground_truth(X, Qt, k, bufs[0].device)
+    qt = torch.from_numpy(Qt).cuda()
+    info = {"train_queries": int(Qt.shape[0]), "models": {}}
+    sweep = []
+    best = None
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for ef_max in args.stop_efs:
+        f, tk, _, cnt, tids, _, _ = ix.search_trace(qt, k, ef_max, 128, period=args.stop_period, rerank=rerank)
+        f, tk, cnt = f.cpu().numpy(), tk.cpu().numpy().view(np.uint32), cnt.cpu().numpy()
+        tids = tids.cpu().numpy().view(np.uint32)
+        mask, y = stopnet.labels_from_trace(tk, cnt, tids, gt_t)
+        norm, w, ls = stopnet.train_from_trace(f, mask, y, epochs=args.stop_epochs, batch=4096)
+        info["models"][ef_max] = {"samples": int(mask.sum()), "positive_frac": float(y[mask].mean()),
+                                  "loss_first": float(ls[0]), "loss_last": float(ls[-1])}
+        ix.set_stop_model(norm, w)
+        for thr in args.stop_thresholds:
+            cand = {"ef": ef_max, "rerank": rerank, "thr": thr, "period": args.stop_period}
+            _search(ix, args, bufs, cand)
+            torch.cuda.synchronize()
+            r = recall_at(bufs[1].cpu().numpy().view(np.uint32), gt)
+            sv = bufs[3].cpu().numpy().view(np.uint32)
+            exp0, stopped = round(float(sv[:, 1].mean()), 2), round(float(((sv[:, 3] & 2) > 0).mean()), 3)
+            if r < args.target_recall:
+                sweep.append((ef_max, thr, r, None, exp0, stopped))
+                continue
+            t, _ = time_form(args, ix, cand, bufs, 5, 1, flush)
+            ms = statistics.median(t)
+            sweep.append((ef_max, thr, r, round(ms, 4), exp0, stopped))
+            if best is None or ms < best[0]:
+                best = (ms, dict(cand, recall=r), (norm, w))
+    log(f"form stop: sweep {sweep}")
+    setting = None
+    if best is not None:
+        setting = best[1]
+        ix.set_stop_model(*best[2])
+    return {"storage": "bf16", "rerank": rerank, "sweep": sweep, "setting": setting, "training": info}
+
+
+def _search(ix, args, bufs, setting, visited_log2=0):
+    q, ids, ds, st = bufs
+    ix.search_into(q, args.k, setting["ef"], ids, ds, st, rerank=setting["rerank"], visited_log2=visited_log2,
+                   stop_threshold=setting.get("thr", 2.0), stop_period=setting.get("period", 0))
+
+
+def time_form(args, ix, setting, bufs, steps, warmup, flush):
     import torch
     q, ids, ds, st = bufs
-    k = args.k
     s = torch.cuda.current_stream()
     for _ in range(warmup):
         flush.zero_()
-        ix.search_into(q, k, ef, ids, ds, st, rerank=rerank)
+        _search(ix, args, bufs, setting)
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for e0, e1 in evs:
         flush.zero_()
         e0.record(s)
-        ix.search_into(q, k, ef, ids, ds, st, rerank=rerank)
+        _search(ix, args, bufs, setting)
         e1.record(s)
     torch.cuda.synchronize()
     times = [e0.elapsed_time(e1) for e0, e1 in evs]
@@ -235,18 +300,16 @@ def algorithmic_bytes(info, stats, k, ef, rerank, d):
                                 "n_stepU": float(n_up.mean()), "bytes_per_query": float(per_q.mean())}
 
 
-def exact_counters(args, ix, ef, rerank, bufs):
+def exact_counters(args, ix, setting, bufs):
     """Per-query counters of one search with a visited set large enough that
     it never forgets (2^14 slots per query); same results, exact evaluations."""
     import torch
-    q, ids, ds, st = bufs
-    ix.search_into(q, args.k, ef, ids, ds, st, rerank=rerank, visited_log2=14)
+    _search(ix, args, bufs, setting, visited_log2=14)
     torch.cuda.synchronize()
-    s = st.cpu().numpy().view(np.uint32).copy()
-    return s
+    return bufs[3].cpu().numpy().view(np.uint32).copy()
 
 
-def e2e_host(args, ix, ef, rerank, Q, steps):
+def e2e_host(args, ix, setting, Q, steps):
     """The same search through the C ABI with pinned HOST buffers: the call
     copies the queries in, searches and copies ids/dists back each step."""
     import torch
@@ -254,12 +317,13 @@ def e2e_host(args, ix, ef, rerank, Q, steps):
     qh = torch.from_numpy(Q).pin_memory()
     ih = torch.empty((n, k), dtype=torch.int32).pin_memory()
     dh = torch.empty((n, k), dtype=torch.float32).pin_memory()
-    ix.search_into(qh, k, ef, ih, dh, None, rerank=rerank)
+    hb = (qh, ih, dh, None)
+    _search(ix, args, hb, setting)
     torch.cuda.synchronize()
     t = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        ix.search_into(qh, k, ef, ih, dh, None, rerank=rerank)  # synchronous for host buffers
+        _search(ix, args, hb, setting)  # synchronous for host buffers
         t.append(time.perf_counter() - t0)
     return n / statistics.mean(t), int(qh.numel() * 4), int(ih.numel() * 4 + dh.numel() * 4)
 
@@ -342,25 +406,26 @@ def main():
     if rank != 0:
         blob, _ = graph_blob(args, X, u, log)
     gt = ground_truth(X, Q, args.k, torch.device("cuda", local))
-    forms, indexes, bufs = run_forms(args, blob, Q, gt, log)
-    ok = {n: f for n, f in forms.items() if f["ef"] is not None}
+    forms, indexes, bufs = run_forms(args, blob, X, Q, gt, log)
+    ok = {n: f for n, f in forms.items() if f["setting"] is not None}
     if "f32" not in ok:
         raise SystemExit("plain form never reached the target recall")
-    # chosen form: the fastest reduced-precision form at the target recall
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     timing = {}
     for name, f in ok.items():
-        t, stats = time_form(args, indexes[name], f["ef"], f["rerank"], bufs, max(3, args.steps // 2), 2, flush)
+        t, _ = time_form(args, indexes[name], f["setting"], bufs, max(3, args.steps // 4), 2, flush)
         timing[name] = statistics.mean(t)
+    # chosen form: the fastest non-plain form at the target recall
     cands = [n for n in ok if n != "f32"] or ["f32"]
     chosen = min(cands, key=lambda n: timing[n])
     fc = ok[chosen]
+    sc = fc["setting"]
     # ---- timed region ----------------------------------------------------
     clocks = Clocks(local, enabled=not args.no_clocks and rank == 0)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    times, stats = time_form(args, indexes[chosen], fc["ef"], fc["rerank"], bufs, args.steps, args.warmup, flush)
+    times, stats = time_form(args, indexes[chosen], sc, bufs, args.steps, args.warmup, flush)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -373,17 +438,19 @@ def main():
     n = Q.shape[0]
     value = n * world / (ms / 1e3)
     # plain form beside it
-    tp, stats_p = time_form(args, indexes["f32"], ok["f32"]["ef"], False, bufs, args.steps, args.warmup, flush)
+    sp = ok["f32"]["setting"]
+    tp, stats_p = time_form(args, indexes["f32"], sp, bufs, args.steps, args.warmup, flush)
     ms_p = statistics.mean(tp)
     info = indexes[chosen].info
     # algorithmic bytes: the counters of one run with an exact (non-forgetting)
     # visited set, so that repeated evaluations of the lossy set are not counted
-    ex_c = exact_counters(args, indexes[chosen], fc["ef"], fc["rerank"], bufs)
-    ex_p = exact_counters(args, indexes["f32"], ok["f32"]["ef"], False, bufs)
-    ab, cnt = algorithmic_bytes(info, ex_c, args.k, fc["ef"], fc["rerank"], X.shape[1])
-    ab_p, cnt_p = algorithmic_bytes(indexes["f32"].info, ex_p, args.k, ok["f32"]["ef"], False, X.shape[1])
+    ex_c = exact_counters(args, indexes[chosen], sc, bufs)
+    ex_p = exact_counters(args, indexes["f32"], sp, bufs)
+    ab, cnt = algorithmic_bytes(info, ex_c, args.k, sc["ef"], sc["rerank"], X.shape[1])
+    ab_p, cnt_p = algorithmic_bytes(indexes["f32"].info, ex_p, args.k, sp["ef"], False, X.shape[1])
     cnt["repeat_eval_frac"] = float(stats[:, 0].astype(np.float64).sum() / ex_c[:, 0].astype(np.float64).sum() - 1)
     cnt_p["repeat_eval_frac"] = float(stats_p[:, 0].astype(np.float64).sum() / ex_p[:, 0].astype(np.float64).sum() - 1)
+    cnt["stopped_early_frac"] = float((stats[:, 3] & 2).astype(bool).mean())
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -391,10 +458,10 @@ def main():
     achieved = ab / (ms / 1e3) / 1e9
     achieved_p = ab_p / (ms_p / 1e3) / 1e9
     traffic, sha = load_traffic(f"hnsw_search_kernel:{chosen}")
-    e2e_v, h2d, d2h = e2e_host(args, indexes[chosen], fc["ef"], fc["rerank"], Q, max(3, args.steps // 2))
+    e2e_v, h2d, d2h = e2e_host(args, indexes[chosen], sc, Q, max(3, args.steps // 4))
     if rank != 0:
         return
-    cpu, _ = oracle_leg(blob, Q, gt, args.k, ok["f32"]["ef"], args.cpu_seconds)
+    cpu, _ = oracle_leg(blob, Q, gt, args.k, sp["ef"], args.cpu_seconds)
     out = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -411,13 +478,15 @@ def main():
         "config": {
             "workload": f"SIFT-shaped {n}-query batch over {args.n_base}x{X.shape[1]} integer-valued vectors, "
                         "squared L2, M=16 Mmax0=32 efC=200, k=10",
-            "form": chosen, "storage": fc["storage"], "rerank": fc["rerank"], "ef": fc["ef"],
-            "recall_at_10": dict(fc["sweep"])[fc["ef"]],
-            "plain_f32": {"ef": ok["f32"]["ef"], "qps": round(n * world / (ms_p / 1e3), 1),
-                          "ms_per_step": round(ms_p, 4), "recall_at_10": dict(ok["f32"]["sweep"])[ok["f32"]["ef"]],
+            "form": chosen, "storage": fc["storage"], "rerank": fc["rerank"], "setting": sc,
+            "recall_at_10": sc["recall"],
+            "plain_f32": {"ef": sp["ef"], "qps": round(n * world / (ms_p / 1e3), 1),
+                          "ms_per_step": round(ms_p, 4), "recall_at_10": sp["recall"],
                           "roofline_frac": round(achieved_p / peak, 4), "achieved_gbs": round(achieved_p, 1),
                           "counters": cnt_p},
-            "forms": {k2: {"ef": v["ef"], "sweep": v["sweep"], "ms_per_step": round(timing.get(k2, 0), 4)}
+            "chosen_vs_plain_qps": round(ms_p / ms, 4),
+            "forms": {k2: {"setting": v["setting"], "sweep": v["sweep"], "ms_per_step": round(timing.get(k2, 0), 4),
+                           **({"training": v["training"]} if "training" in v else {})}
                       for k2, v in forms.items()},
             "l2": "flushed between timed steps (512 MB device write, outside the events)",
             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
@@ -443,7 +512,7 @@ def profile_run(args, X, Q, u, log):
     import torch
     from paper_1603_09320_gb300 import hnsw
     blob, _ = graph_blob(args, X, u, log)
-    storage, keep, rerank = FORMS[args.profile_form]
+    storage, keep, rerank, _stop = FORMS[args.profile_form]
     ix = hnsw.Index(blob, storage, keep_fp32=keep)
     q = torch.from_numpy(Q).cuda()
     n, k = Q.shape[0], args.k

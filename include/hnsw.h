@@ -170,8 +170,14 @@ typedef struct {
                                 network's sigmoid exceeds it (needs hnsw_set_stop_model);
                                 <= 0 or >= 1: off, the plain search */
     int32_t stop_period;     /* learned stop / trace: check every stop_period layer-0
-                                expansions (<= 0: 4) */
-    int32_t reserved[2];
+                                expansions (<= 0: 8 for the stop, 4 for traces) */
+    int32_t schedule;        /* 0: automatic -- batches larger than four times the kernel's
+                                resident warps run in two passes, the upper-layer descent of all
+                                queries first, then the layer-0 beams in order of
+                                decreasing descent distance (long searches start first,
+                                results unchanged; uses stream-ordered scratch);
+                                1: one pass in input order; 2: always two passes */
+    int32_t reserved;
 } hnsw_search_params;
 
 /* hnsw_search with the options above and optional per-query counters

@@ -108,6 +108,13 @@ struct SearchArgs {
     float* tr_logit;     // [n][tr_max] (only with a model)
     int32_t* tr_count;   // [n] checks recorded
     int tr_max;
+    // two-pass scheduling: mode 0 = descent and beam per query in input order;
+    // mode 1 = descent only, writing the layer-0 enter key and the upper-layer
+    // counters of every query; mode 2 = beam only, queries taken in `order`
+    int mode;
+    uint64_t* ep_keys;   // [n]
+    uint32_t* up_cnt;    // [n][2]: distance evaluations, rows read on layers >= 1
+    const uint32_t* order;
 };
 
 // ---- keys -----------------------------------------------------------------
@@ -150,11 +157,22 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Row gathers are random and not reused by this SM: keep them out of L1 so
+// that L1 holds what is reused (the stop network's weights).
+#ifndef HNSW_ROW_NO_L1
+#define HNSW_ROW_NO_L1 0
+#endif
 __device__ __forceinline__ uint4 ld_row_chunk(const uint4* p) {
     uint4 v;
+#if HNSW_ROW_NO_L1
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+#else
     asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                  : "l"(p));
+#endif
     return v;
 }
 
@@ -475,7 +493,7 @@ __device__ __forceinline__ uint32_t ix_row32(const SearchArgs& a) { return a.ix.
 // STOP: the build with learned-stop checks and trace recording (the plain
 // search is compiled without them and keeps its smaller register budget).
 template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP>
-__global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 8) : 0) hnsw_search_kernel(const SearchArgs a) {
     using D = Dist<ST, TEAM, CPL, U, FULL>;
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -490,12 +508,12 @@ __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
     uint32_t* nbuf = reinterpret_cast<uint32_t*>(qs + ix_row32(a));  // staged neighbour row (16-byte aligned)
     const DevIndex& ix = a.ix;
     const int hsz = 1 << a.hlog;
-
     for (;;) {
         uint32_t qi = 0;
         if (lane == 0) qi = atomicAdd(a.work, 1u);
         qi = __shfl_sync(kFull, qi, 0);
         if (qi >= a.n) break;
+        if (a.mode == 2) qi = __ldg(a.order + qi);
         const float* qp = a.q + uint64_t(qi) * ix.d;
         float qr[D::QF];
         D::load_q(qp, ix.d, qr, lane);
@@ -508,12 +526,18 @@ __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
         int size = 0;
         __syncwarp();
         if (ix.N > 0) {
+            uint64_t cur = 0;
+            if (a.mode == 2) {  // the descent ran in the first pass
+                cur = a.ep_keys[qi];
+                n_eval = a.up_cnt[2 * uint64_t(qi)];
+                n_stepU = a.up_cnt[2 * uint64_t(qi) + 1];
+            } else {
             // enter point and greedy descent (Alg. 5 lines 2-6)
             if (lane == 0) ids[0] = ix.ep;
             __syncwarp();
             D::run(ix, qr, ids, 1, dst, lane);
             __syncwarp();
-            uint64_t cur = mkkey(dst[0], ix.ep);
+            cur = mkkey(dst[0], ix.ep);
             n_eval = 1;
             for (int lc = ix.maxlevel; lc >= 1; --lc) {
                 for (;;) {
@@ -543,6 +567,16 @@ __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
                         break;
                     }
                 }
+            }
+            }
+            if (a.mode == 1) {  // first pass: keep the layer-0 enter point for the second
+                if (lane == 0) {
+                    a.ep_keys[qi] = cur;
+                    a.up_cnt[2 * uint64_t(qi)] = n_eval;
+                    a.up_cnt[2 * uint64_t(qi) + 1] = n_stepU;
+                }
+                __syncwarp();
+                continue;
             }
             // layer 0 beam (Alg. 2 with ef')
             if (lane == 0) {
@@ -661,7 +695,7 @@ __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
                         f[3] = log1pf(fmaxf(d1, 0.0f));
                         f[4] = log1pf(float(stale));
                         f[5] = log1pf(fmaxf(key_dist(W[a.k - 1]) / d1n, 0.0f));
-                        const float logit = a.stop ? stop_logit(a.stop, f, lane) : 0.0f;
+                        const float logit = a.stop ? stop_logit(a.stop, f, reinterpret_cast<float*>(ck), lane) : 0.0f;
                         if (a.tr_count) {
                             if (n_checks < a.tr_max) {
                                 const uint64_t slot = uint64_t(qi) * uint64_t(a.tr_max) + uint64_t(n_checks);
@@ -720,6 +754,41 @@ __global__ void HNSW_SEARCH_BOUNDS hnsw_search_kernel(const SearchArgs a) {
         }
         __syncwarp();
     }
+}
+
+// ---- ordering of the second pass --------------------------------------------
+// Queries whose upper-layer descent ends far from them tend to need more
+// layer-0 expansions; starting them first shortens the tail of the batch
+// (longest-first list scheduling).  One block sorts a chunk of up to
+// kSortChunk queries by descending descent distance (bitonic sort of
+// (~ord(d1), query) keys in shared memory); chunks are sorted independently.
+constexpr int kSortChunk = 16384;
+
+__global__ void __launch_bounds__(1024) order_by_descent(const uint64_t* __restrict__ ep_keys, uint32_t n,
+                                                        uint32_t* __restrict__ order) {
+    extern __shared__ __align__(16) uint64_t sk[];
+    const uint32_t base = blockIdx.x * uint32_t(kSortChunk);
+    const uint32_t m = min(uint32_t(kSortChunk), n - base);
+    uint32_t P = 1;
+    while (P < m) P <<= 1;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+        sk[i] = i < m ? ((uint64_t(~uint32_t(ep_keys[base + i] >> 32)) << 32) | uint64_t(base + i)) : ~0ull;
+    __syncthreads();
+    for (uint32_t kk = 2; kk <= P; kk <<= 1)
+        for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint32_t q = i ^ j;
+                if (q > i) {
+                    const uint64_t x = sk[i], y = sk[q];
+                    if ((x > y) == ((i & kk) == 0)) {
+                        sk[i] = y;
+                        sk[q] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) order[base + i] = uint32_t(sk[i]);
 }
 
 // ---- host side --------------------------------------------------------------
@@ -797,9 +866,10 @@ int auto_visited_log2(int efp) {
     return l < 10 ? 10 : (l > 13 ? 13 : l);
 }
 
-hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n,
-                          uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
-                          uint32_t* work, const StopModel* stop) {
+hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n,
+                               uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
+                               uint32_t* work, const StopModel* stop, int mode, uint64_t* ep_keys,
+                               uint32_t* up_cnt, const uint32_t* order) {
     const DevIndex& D = ix->dev;
     KernelChoice kc;
     if (!choose_kernel(D.storage, D.row_chunks, stop != nullptr && stop->period > 0, kc))
@@ -817,6 +887,10 @@ hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const flo
     a.out_dists = dists;
     a.stats = stats;
     a.work = work;
+    a.mode = mode;
+    a.ep_keys = ep_keys;
+    a.up_cnt = up_cnt;
+    a.order = order;
     if (stop) {
         a.stop = static_cast<const StopDev*>(stop->stop);
         a.stop_logit = stop->logit_threshold;
@@ -851,6 +925,30 @@ hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const flo
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("search launch: ") + cudaGetErrorString(e));
     return HNSW_OK;
+}
+
+hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n,
+                          uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
+                          uint32_t* work, const StopModel* stop) {
+    return launch_search_mode(ix, p, q, n, ids, dists, stats, s, work, stop, 0, nullptr, nullptr, nullptr);
+}
+
+// A pair of work counters for one call (slots 2i and 2i+1 of the index's
+// ring): concurrent calls on one index use different counters.
+uint32_t take_work_slots(hnsw_index* ix) {
+    return (ix->work_next.fetch_add(1) % uint32_t(kWorkSlots / 2)) * 2u;
+}
+
+// Resident warps of the search kernel (about 7 blocks per SM x 4 warps x SMs).
+// Measured on SIFT-shaped 1M, the two-pass order gains a few percent only when
+// a batch is several times larger than this (at 10,000 queries the separate
+// descent pass costs more than the ordering saves), so the automatic choice
+// uses it above four times this count.
+uint32_t resident_warps(const hnsw_index* ix) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return uint32_t(sms) * 28u;
 }
 
 }  // namespace hnswgb
@@ -904,9 +1002,8 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
         sp += al256(ob);
         if (!ds) st = reinterpret_cast<hnsw_query_stats*>(sp);
     }
-    const uint32_t slot = ix->work_next.fetch_add(1) % kWorkSlots;
-    uint32_t* work = ix->d_work + slot;
-    cudaError_t e = cudaMemsetAsync(work, 0, 4, s);
+    uint32_t* work = ix->d_work + take_work_slots(ix);
+    cudaError_t e = cudaMemsetAsync(work, 0, 8, s);
     if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search: memset: ") + cudaGetErrorString(e));
     StopModel sm{};
     const StopModel* smp = nullptr;
@@ -914,11 +1011,46 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
         if (!ix->d_stop) return fail(HNSW_EINVAL, "hnsw_search: stop_threshold in (0,1) needs a stop model");
         sm.stop = ix->d_stop;
         sm.logit_threshold = logf(p->stop_threshold / (1.0f - p->stop_threshold));
-        sm.period = p->stop_period > 0 ? p->stop_period : 4;
+        sm.period = p->stop_period > 0 ? p->stop_period : 8;
         smp = &sm;
     }
-    hnsw_status r = launch_search(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp);
-    if (r != HNSW_OK) return r;
+    // schedule: 0 automatic (two passes when the batch exceeds the resident
+    // warps), 1 one pass in input order, 2 always two passes
+    const bool two =
+        ix->dev.N > 0 && (p->schedule == 2 || (p->schedule == 0 && uint64_t(n) > 4ull * resident_warps(ix)));
+    hnsw_status r = HNSW_OK;
+    if (!two) {
+        r = launch_search(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp);
+        if (r != HNSW_OK) return r;
+    } else {
+        // stream-ordered scratch: enter keys [n] u64, upper counters [n][2] u32, order [n] u32
+        void* scr = nullptr;
+        const size_t bk = al256(size_t(n) * 8), bc = al256(size_t(n) * 8), bo = al256(size_t(n) * 4);
+        e = cudaMallocAsync(&scr, bk + bc + bo, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HNSW_ENOMEM, "hnsw_search: scheduling scratch");
+        }
+        uint64_t* keys = static_cast<uint64_t*>(scr);
+        uint32_t* cnt = reinterpret_cast<uint32_t*>(static_cast<char*>(scr) + bk);
+        uint32_t* ord = reinterpret_cast<uint32_t*>(static_cast<char*>(scr) + bk + bc);
+        r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 1, keys, cnt, nullptr);
+        if (r == HNSW_OK) {
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(order_by_descent, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortChunk * 8);
+                attr = true;
+            }
+            const unsigned chunks = unsigned((uint64_t(n) + kSortChunk - 1) / kSortChunk);
+            order_by_descent<<<chunks, 1024, kSortChunk * 8, s>>>(keys, uint32_t(n), ord);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) r = fail(HNSW_ECUDA, std::string("hnsw_search: order: ") + cudaGetErrorString(e));
+        }
+        if (r == HNSW_OK)
+            r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work + 1, smp, 2, keys, cnt, ord);
+        cudaFreeAsync(scr, s);
+        if (r != HNSW_OK) return r;
+    }
     if (!di || !dd || !ds) {
         if (!di) cudaMemcpyAsync(out_ids, ids, ob, cudaMemcpyDeviceToHost, s);
         if (!dd) cudaMemcpyAsync(out_dists, dists, ob, cudaMemcpyDeviceToHost, s);
@@ -965,9 +1097,8 @@ extern "C" hnsw_status hnsw_search_trace(hnsw_index* ix, const hnsw_search_param
     sm.tr_logit = ix->d_stop ? logits : nullptr;
     sm.tr_count = n_checks;
     sm.tr_max = max_checks;
-    const uint32_t slot = ix->work_next.fetch_add(1) % kWorkSlots;
-    uint32_t* work = ix->d_work + slot;
-    cudaError_t e = cudaMemsetAsync(work, 0, 4, s);
+    uint32_t* work = ix->d_work + take_work_slots(ix);
+    cudaError_t e = cudaMemsetAsync(work, 0, 8, s);
     if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search_trace: memset: ") + cudaGetErrorString(e));
     hnsw_search_params q = *p;
     return launch_search(ix, q, queries, uint32_t(n), out_ids, out_dists, stats, s, work, &sm);

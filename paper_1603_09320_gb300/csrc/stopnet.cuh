@@ -35,10 +35,28 @@ struct StopDev {
     float pad[3];
     __half2 w2p[kStopH * 32];
 };
+static_assert(sizeof(StopDev) % 16 == 0, "StopDev is copied in 16-byte words");
+
+// read-only load kept in L1 in preference to streaming data
+__device__ __forceinline__ float4 ld_w4(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::evict_last.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned ld_w1(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
 
 // Logit of the network for features f (identical in every lane), computed by
-// one warp: lane l owns hidden units l and l + 32.
-__device__ __forceinline__ float stop_logit(const StopDev* __restrict__ m, const float (&f)[kStopIn], int lane) {
+// one warp: lane l owns hidden units l and l + 32.  The first hidden layer is
+// exchanged through a 64-float scratch `hs` in shared memory and read back
+// with 16-byte broadcast loads.
+__device__ __forceinline__ float stop_logit(const StopDev* __restrict__ m, const float (&f)[kStopIn],
+                                            float* hs, int lane) {
     float xn[kStopIn];
 #pragma unroll
     for (int i = 0; i < kStopIn; ++i) xn[i] = (f[i] - __ldg(&m->mu[i])) * __ldg(&m->isig[i]);
@@ -48,19 +66,26 @@ __device__ __forceinline__ float stop_logit(const StopDev* __restrict__ m, const
         ha = fmaf(__ldg(&m->w1[lane * kStopIn + i]), xn[i], ha);
         hb = fmaf(__ldg(&m->w1[(lane + 32) * kStopIn + i]), xn[i], hb);
     }
-    ha = fmaxf(ha, 0.0f);
-    hb = fmaxf(hb, 0.0f);
+    __syncwarp();
+    hs[lane] = fmaxf(ha, 0.0f);
+    hs[lane + 32] = fmaxf(hb, 0.0f);
+    __syncwarp();
     float za = __ldg(&m->b2[lane]), zb = __ldg(&m->b2[lane + 32]);
     const unsigned* w2 = reinterpret_cast<const unsigned*>(m->w2p);
-#pragma unroll 8
-    for (int u = 0; u < kStopH; ++u) {
-        const float hu = __shfl_sync(0xffffffffu, u < 32 ? ha : hb, u & 31);
-        const unsigned bits = __ldg(w2 + u * 32 + lane);
-        __half2 w;
-        memcpy(&w, &bits, 4);
-        const float2 wf = __half22float2(w);
-        za = fmaf(wf.x, hu, za);
-        zb = fmaf(wf.y, hu, zb);
+    const float4* h4 = reinterpret_cast<const float4*>(hs);
+#pragma unroll 4
+    for (int u4 = 0; u4 < kStopH / 4; ++u4) {
+        const float4 h = h4[u4];
+        const float hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned bits = ld_w1(w2 + (u4 * 4 + j) * 32 + lane);
+            __half2 w;
+            memcpy(&w, &bits, 4);
+            const float2 wf = __half22float2(w);
+            za = fmaf(wf.x, hv[j], za);
+            zb = fmaf(wf.y, hv[j], zb);
+        }
     }
     float o = __ldg(&m->w3[lane]) * fmaxf(za, 0.0f) + __ldg(&m->w3[lane + 32]) * fmaxf(zb, 0.0f);
 #pragma unroll

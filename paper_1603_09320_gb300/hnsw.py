@@ -43,7 +43,8 @@ class IndexInfo(C.Structure):
 
 class SearchParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("ef", C.c_int32), ("rerank", C.c_int32), ("visited_log2", C.c_int32),
-                ("stop_threshold", C.c_float), ("stop_period", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("stop_threshold", C.c_float), ("stop_period", C.c_int32), ("schedule", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class StopTrainParams(C.Structure):
@@ -214,10 +215,10 @@ class Index:
 
     def search_into(self, queries, k: int, ef: int, out_ids, out_dists, stats=None, rerank: bool = False,
                     visited_log2: int = 0, stop_threshold: float = 2.0, stop_period: int = 0,
-                    stream=None) -> None:
+                    schedule: int = 0, stream=None) -> None:
         """hnsw_search_ex into caller-owned buffers (host or device)."""
         n = int(queries.shape[0]) if queries is not None else 0
-        p = SearchParams(k, ef, int(rerank), visited_log2, stop_threshold, stop_period)
+        p = SearchParams(k, ef, int(rerank), visited_log2, stop_threshold, stop_period, schedule)
         qp, _a = _ptr(queries)
         ip, _b = _ptr(out_ids)
         dp, _c = _ptr(out_dists)
@@ -225,7 +226,7 @@ class Index:
         _check(lib().hnsw_search_ex(self.h, C.byref(p), qp, n, ip, dp, sp, _stream_ptr(stream)))
 
     def search(self, queries, k: int, ef: int, rerank: bool = False, stats: bool = False, visited_log2: int = 0,
-               stop_threshold: float = 2.0, stop_period: int = 0, stream=None):
+               stop_threshold: float = 2.0, stop_period: int = 0, schedule: int = 0, stream=None):
         """Returns (ids, dists[, stats]) as arrays/tensors on the queries' device."""
         if hasattr(queries, "is_cuda") and queries.is_cuda:
             import torch
@@ -240,7 +241,7 @@ class Index:
             ds = np.empty((n, k), dtype=np.float32)
             st = np.empty((n, 4), dtype=np.uint32) if stats else None
         self.search_into(queries, k, ef, ids, ds, st, rerank=rerank, visited_log2=visited_log2,
-                         stop_threshold=stop_threshold, stop_period=stop_period, stream=stream)
+                         stop_threshold=stop_threshold, stop_period=stop_period, schedule=schedule, stream=stream)
         return (ids, ds, st) if stats else (ids, ds)
 
 
