@@ -261,6 +261,60 @@ hnsw_status hnsw_stop_train(const float* x, const float* y, int64_t n, const hns
 hnsw_status hnsw_search_noalloc(hnsw_index* index, const float* queries, int64_t n, int32_t k, int32_t ef,
                                 uint32_t* out_ids, float* out_dists, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching over resident indexes (an addition; the      */
+/* paper has no serving component)                                           */
+/* ------------------------------------------------------------------------ */
+/* A server owns `n_slots` CUDA streams ("slots") and one device arena of
+ * `memory_budget` bytes (0: a quarter of the free device memory, at most
+ * 4 GiB).  Submitted requests wait in a FIFO; the request at its head is
+ * admitted as soon as a slot is free and its device buffers (queries n*d*4
+ * bytes, ids and distances n*k*4 bytes each, 256-byte aligned) fit in the
+ * arena.  Requests admitted while others are on the GPU run concurrently
+ * with them.  Results go to the caller's host buffers, which must stay valid
+ * until hnsw_server_wait returns for the ticket.  Indexes stay resident and
+ * owned by the caller (free them after hnsw_server_destroy). */
+typedef struct hnsw_server hnsw_server;
+
+typedef struct {
+    int32_t n_slots;          /* 1..64 concurrent requests on the device */
+    uint64_t memory_budget;   /* device bytes for request buffers, 0: automatic */
+} hnsw_server_params;
+
+typedef struct {
+    int32_t index;            /* id returned by hnsw_server_add_index */
+    int64_t n;                /* queries in this request (>= 1) */
+    int32_t k, ef, rerank;    /* as in hnsw_search_params */
+    float stop_threshold;     /* learned stop, as in hnsw_search_params */
+    int32_t stop_period;
+    const float* queries;     /* host [n][d] */
+    uint32_t* out_ids;        /* host [n][k] */
+    float* out_dists;         /* host [n][k] */
+} hnsw_request;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t queued, in_flight;          /* waiting for admission / on the device */
+    uint64_t bytes_in_use, budget;       /* device arena */
+} hnsw_server_stats;
+
+hnsw_status hnsw_server_create(const hnsw_server_params* params, hnsw_server** out);
+hnsw_status hnsw_server_add_index(hnsw_server* server, hnsw_index* index, int32_t* index_id);
+/* Errors: HNSW_EINVAL (bad request, unknown index, larger than the whole
+ * budget), HNSW_EBUSY (server stopping). */
+hnsw_status hnsw_server_submit(hnsw_server* server, const hnsw_request* request, uint64_t* ticket);
+hnsw_status hnsw_server_poll(hnsw_server* server, uint64_t ticket, int32_t* done);
+/* Waits until the request's results are in the caller's buffers (timeout_ms
+ * < 0: no limit; HNSW_ETIMEOUT when it runs out, the request continues).  On
+ * return other than HNSW_ETIMEOUT the ticket is consumed; latency_ms (may be
+ * NULL) receives submit-to-completion time.  A request that failed on the
+ * device returns its error here. */
+hnsw_status hnsw_server_wait(hnsw_server* server, uint64_t ticket, int32_t timeout_ms, double* latency_ms);
+hnsw_status hnsw_server_get_stats(hnsw_server* server, hnsw_server_stats* out);
+/* Completes every submitted request, then releases the server's streams and
+ * arena. */
+hnsw_status hnsw_server_destroy(hnsw_server* server);
+
 /* Thread-local message describing the last failure of this thread. */
 const char* hnsw_last_error(void);
 

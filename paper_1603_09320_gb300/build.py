@@ -22,9 +22,9 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
             "-I", INCLUDE]
-CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE]
+CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", "/usr/local/cuda/include"]
 
-SOURCES = ["search.cu", "search_noalloc.cu", "index.cu", "stopnet.cu", "builder.cpp", "blob.cpp"]
+SOURCES = ["search.cu", "search_noalloc.cu", "index.cu", "stopnet.cu", "builder.cpp", "blob.cpp", "server.cpp"]
 HEADERS = ["common.hpp", "index.cuh", "stopnet.cuh"]
 
 

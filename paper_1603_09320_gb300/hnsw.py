@@ -52,6 +52,22 @@ class StopTrainParams(C.Structure):
                 ("beta2", C.c_float), ("eps", C.c_float), ("weight_decay", C.c_float), ("seed", C.c_uint64)]
 
 
+class ServerParams(C.Structure):
+    _fields_ = [("n_slots", C.c_int32), ("memory_budget", C.c_uint64)]
+
+
+class Request(C.Structure):
+    _fields_ = [("index", C.c_int32), ("n", C.c_int64), ("k", C.c_int32), ("ef", C.c_int32), ("rerank", C.c_int32),
+                ("stop_threshold", C.c_float), ("stop_period", C.c_int32), ("queries", C.c_void_p),
+                ("out_ids", C.c_void_p), ("out_dists", C.c_void_p)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("queued", C.c_uint64), ("in_flight", C.c_uint64), ("bytes_in_use", C.c_uint64),
+                ("budget", C.c_uint64)]
+
+
 class QueryStats(C.Structure):
     _fields_ = [("n_eval", C.c_uint32), ("n_exp0", C.c_uint32), ("n_stepU", C.c_uint32), ("flags", C.c_uint32)]
 
@@ -88,6 +104,13 @@ def lib():
             "hnsw_stop_grad": (i32, [vp, vp, i64, vp, vp, vp, vp, vp]),
             "hnsw_stop_train": (i32, [vp, vp, i64, C.POINTER(StopTrainParams), vp, vp, vp, vp, vp]),
             "hnsw_abi_version": (i32, []),
+            "hnsw_server_create": (i32, [C.POINTER(ServerParams), C.POINTER(vp)]),
+            "hnsw_server_add_index": (i32, [vp, vp, C.POINTER(i32)]),
+            "hnsw_server_submit": (i32, [vp, C.POINTER(Request), C.POINTER(u64)]),
+            "hnsw_server_poll": (i32, [vp, u64, C.POINTER(i32)]),
+            "hnsw_server_wait": (i32, [vp, u64, i32, C.POINTER(C.c_double)]),
+            "hnsw_server_get_stats": (i32, [vp, C.POINTER(ServerStats)]),
+            "hnsw_server_destroy": (i32, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -267,3 +290,64 @@ def stop_train(x, y, w_init, epochs: int = 20, batch: int = 4096, lr: float = 2e
     _check(lib().hnsw_stop_train(x.data_ptr(), y.data_ptr(), x.shape[0], C.byref(p), w0.ctypes.data,
                                  norm.ctypes.data, w.ctypes.data, ls.ctypes.data, _stream_ptr(None)))
     return norm, w.view(np.float16), ls
+
+
+class Server:
+    """Continuous-batching request loop over resident indexes (hnsw_server_*).
+    Query and result buffers are numpy arrays kept alive until wait()."""
+
+    def __init__(self, n_slots: int = 8, memory_budget: int = 0):
+        h = C.c_void_p()
+        _check(lib().hnsw_server_create(C.byref(ServerParams(n_slots, memory_budget)), C.byref(h)))
+        self.h = h
+        self._live = {}
+
+    def add_index(self, index: Index) -> int:
+        i = C.c_int32()
+        _check(lib().hnsw_server_add_index(self.h, index.h, C.byref(i)))
+        return int(i.value)
+
+    def submit(self, index_id: int, queries, k: int, ef: int, rerank: bool = False, stop_threshold: float = 2.0,
+               stop_period: int = 0) -> int:
+        q = np.ascontiguousarray(queries, dtype=np.float32)
+        n = q.shape[0]
+        ids = np.empty((n, k), dtype=np.uint32)
+        ds = np.empty((n, k), dtype=np.float32)
+        r = Request(index_id, n, k, ef, int(rerank), stop_threshold, stop_period, q.ctypes.data, ids.ctypes.data,
+                    ds.ctypes.data)
+        t = C.c_uint64()
+        _check(lib().hnsw_server_submit(self.h, C.byref(r), C.byref(t)))
+        self._live[int(t.value)] = (q, ids, ds)
+        return int(t.value)
+
+    def poll(self, ticket: int) -> bool:
+        d = C.c_int32()
+        _check(lib().hnsw_server_poll(self.h, ticket, C.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Returns (ids, dists, latency_ms) of a completed request."""
+        lat = C.c_double()
+        st = lib().hnsw_server_wait(self.h, ticket, timeout_ms, C.byref(lat))
+        if st != 0 and st != 5:
+            self._live.pop(ticket, None)
+        _check(st)
+        q, ids, ds = self._live.pop(ticket)
+        return ids, ds, float(lat.value)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().hnsw_server_get_stats(self.h, C.byref(s)))
+        return {f: int(getattr(s, f)) for f, _ in ServerStats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().hnsw_server_destroy(self.h)
+            self.h = None
+        self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

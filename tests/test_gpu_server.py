@@ -1,0 +1,90 @@
+"""Continuous-batching server: mixed requests (index, n, k, ef, storage,
+rerank) submitted while others run on the GPU return exactly what the same
+request returns when searched alone; admission waits for arena memory."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_1603_09320_gb300 import synth
+from _graphs import oracle_graph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    from paper_1603_09320_gb300 import build, hnsw
+    build.build()
+    g1, X1, b1 = oracle_graph("tiny", 10_000)
+    g2, X2, b2 = oracle_graph("sift", 20_000)
+    ixs = [hnsw.Index(b1, "f32"), hnsw.Index(b2, "f32"), hnsw.Index(b2, "bf16", keep_fp32=True)]
+    Qs = [synth.queries("tiny", 2000), synth.queries("sift", 2000), synth.queries("sift", 2000)]
+    yield hnsw, ixs, Qs
+    for ix in ixs:
+        ix.close()
+
+
+def _requests(rng, Qs, n_req):
+    reqs = []
+    for _ in range(n_req):
+        which = int(rng.integers(0, 3))
+        n = int(np.exp(rng.uniform(0, np.log(300))))
+        s = int(rng.integers(0, Qs[which].shape[0] - n))
+        k = int(rng.choice([1, 10, 100]))
+        ef = int(rng.integers(k, 257))
+        reqs.append((which, Qs[which][s:s + n], k, ef, which == 2))
+    return reqs
+
+
+def _alone(ix, q, k, ef, rerank):
+    return ix.search(q, k, ef, rerank=rerank)
+
+
+@pytest.mark.parametrize("slots,budget", [(8, 0), (3, 1 << 20)])
+def test_mixed_requests_equal_alone(setup, slots, budget):
+    hnsw, ixs, Qs = setup
+    rng = np.random.default_rng(slots)
+    reqs = _requests(rng, Qs, 150)
+    sv = hnsw.Server(n_slots=slots, memory_budget=budget)
+    ids_ = [sv.add_index(ix) for ix in ixs]
+    tickets = []
+
+    def submit_half(part):
+        for r in part:
+            tickets.append((r, sv.submit(ids_[r[0]], r[1], r[2], r[3], rerank=r[4])))
+
+    th = [threading.Thread(target=submit_half, args=(reqs[i::2],)) for i in range(2)]
+    for t in th:
+        t.start()
+    peak_queued = 0
+    for t in th:
+        t.join()
+    peak_queued = max(peak_queued, sv.stats()["queued"])
+    lat = []
+    for (which, q, k, ef, rr), t in tickets:
+        ids, ds, ms = sv.wait(t, timeout_ms=60_000)
+        ai, ad = _alone(ixs[which], q, k, ef, rr)
+        np.testing.assert_array_equal(ids, ai)
+        np.testing.assert_array_equal(ds, ad)
+        lat.append(ms)
+    st = sv.stats()
+    sv.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["bytes_in_use"] == 0 and st["in_flight"] == 0 and st["queued"] == 0
+    assert max(lat) > 0
+
+
+def test_request_larger_than_budget_is_rejected(setup):
+    hnsw, ixs, Qs = setup
+    sv = hnsw.Server(n_slots=2, memory_budget=64 * 1024)
+    i = sv.add_index(ixs[1])
+    with pytest.raises(hnsw.HnswError) as e:
+        sv.submit(i, Qs[1][:1000], 10, 32)  # 512 KB of queries > 64 KB budget
+    assert e.value.status == 1
+    t = sv.submit(i, Qs[1][:10], 10, 32)
+    ids, ds, _ = sv.wait(t, timeout_ms=60_000)
+    ai, _ = ixs[1].search(Qs[1][:10], 10, 32)
+    np.testing.assert_array_equal(ids, ai)
+    sv.close()
