@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--stop-epochs", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving mix: SIFT-shaped 1M and GloVe-shaped 1.2M indexes resident, Poisson requests")
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-rate", type=float, default=20_000.0, help="mean requests per second")
     ap.add_argument("--profile-form", default=None,
                     help="profiling run: upload only this form and launch the search --profile-launches times")
     ap.add_argument("--profile-ef", type=int, default=64)
@@ -380,6 +384,8 @@ def main():
 
     if args.impl == "reference":
         return reference_arm(args, rank, world, log)
+    if args.serving:
+        return serving_bench(args, log)
 
     import torch
     torch.cuda.set_device(local)
@@ -505,6 +511,110 @@ def main():
     out["cpu_baseline"]["recall_at_10"] = cpu["recall"]
     out["cpu_baseline"]["oracle_n_dist_mean"] = cpu["n_dist_mean"]
     print(json.dumps(out), flush=True)
+
+
+def serving_bench(args, log):
+    """Serving mix (one GPU): SIFT-shaped 1M x 128 (L2) and GloVe-shaped
+    1.2M x 100 (cosine) indexes resident; Poisson arrivals at the given mean
+    rate; each request a batch of 1..1024 queries (log-uniform) against one
+    index chosen 50/50, k in {1, 10, 100}, ef uniform in [k, 512].  Two server
+    configurations: plain fp32, and bf16 storage with the exact fp32 rerank.
+    Reports queries/s, requests/s, p50/p99 latency and recall@10 (requests
+    with k >= 10) against exact k-NN."""
+    import threading
+    import torch
+    from paper_1603_09320_gb300 import build as B
+    from paper_1603_09320_gb300 import graphs, hnsw, synth
+    B.build()
+    sets = {}
+    for name in ("sift", "glove"):
+        X = synth.base(name)
+        blob, bs = graphs.build_or_load(name, X.shape[0], X=X, log=log)
+        Q = synth.queries(name)
+        gt = ground_truth_metric(X, Q, 10, synth.params(name)["metric"])
+        sets[name] = (blob, Q, gt, bs)
+        del X
+    rng = np.random.default_rng(7)
+    n_req = int(args.serving_rate * args.serving_seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serving_rate, size=n_req))
+    plan = []
+    for i in range(n_req):
+        name = "sift" if rng.random() < 0.5 else "glove"
+        n = min(1024, int(np.exp(rng.uniform(0, np.log(1025)))))
+        s0 = int(rng.integers(0, sets[name][1].shape[0] - n + 1))
+        k = int(rng.choice([1, 10, 100]))
+        ef = int(rng.integers(k, 513))
+        plan.append((name, s0, n, k, ef))
+    out = {"metric": "serving mix: p50/p99 latency and throughput", "data": "synthetic", "n_gpus": 1,
+           "config": {"workload": "SIFT-shaped 1M x 128 L2 + GloVe-shaped 1.2M x 100 cosine, Poisson "
+                                  f"{args.serving_rate:.0f} requests/s for {args.serving_seconds}s, batches 1..1024 "
+                                  "log-uniform, k in {1,10,100}, ef uniform [k,512], index 50/50",
+                      "requests": n_req, "queries": int(sum(p[2] for p in plan)),
+                      "build_seconds": {k2: v[3] for k2, v in sets.items()}}, "variants": {}}
+    for variant, (storage, keep, rerank) in {"plain_f32": ("f32", False, False),
+                                             "bf16_rerank": ("bf16", True, True)}.items():
+        ixs = {name: hnsw.Index(sets[name][0], storage, keep_fp32=keep) for name in sets}
+        sv = hnsw.Server(n_slots=16)
+        ids_ = {name: sv.add_index(ix) for name, ix in ixs.items()}
+        tickets = [None] * n_req
+        t0 = time.perf_counter()
+
+        def producer():
+            for i, (name, s0, n, k, ef) in enumerate(plan):
+                while time.perf_counter() - t0 < arrivals[i]:
+                    pass
+                tickets[i] = sv.submit(ids_[name], sets[name][1][s0:s0 + n], k, ef, rerank=rerank)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        lat = np.zeros(n_req)
+        hits = total = 0
+        for i in range(n_req):
+            while tickets[i] is None:
+                time.sleep(0.0001)
+            ids, ds, ms = sv.wait(tickets[i], timeout_ms=120_000)
+            lat[i] = ms
+            name, s0, n, k, ef = plan[i]
+            if k >= 10:
+                gt = sets[name][2][s0:s0 + n]
+                for j in range(n):
+                    hits += len(set(ids[j, :10].tolist()) & set(gt[j].tolist()))
+                total += n * 10
+        th.join()
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+        sv.close()
+        for ix in ixs.values():
+            ix.close()
+        qn = out["config"]["queries"]
+        out["variants"][variant] = {"queries_per_s": round(qn / wall, 1), "requests_per_s": round(n_req / wall, 1),
+                                    "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                                    "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                                    "mean_ms": round(float(lat.mean()), 3), "wall_s": round(wall, 3),
+                                    "recall_at_10": round(hits / max(total, 1), 5), "failed": st["failed"]}
+        log(f"serving {variant}: {out['variants'][variant]}")
+    print(json.dumps(out), flush=True)
+
+
+def ground_truth_metric(X, Q, k, metric):
+    """Exact k-NN for L2 (as ground_truth) or cosine (largest inner product):
+    fp32 shortlist of 64 on the GPU, fp64 rescoring on the host by key."""
+    if metric == 0:
+        return ground_truth(X, Q, k, "cuda")
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Xd = torch.from_numpy(X).cuda()
+    out = np.zeros((Q.shape[0], k), dtype=np.int64)
+    for s in range(0, Q.shape[0], 1000):
+        q = torch.from_numpy(Q[s:s + 1000]).cuda()
+        cand = torch.topk(q @ Xd.T, 64, dim=1, largest=True).indices.cpu().numpy()
+        for i in range(cand.shape[0]):
+            c = cand[i]
+            ex = 1.0 - (X[c].astype(np.float64) @ Q[s + i].astype(np.float64))
+            out[s + i] = c[np.lexsort((c, ex))[:k]]
+    del Xd
+    torch.cuda.empty_cache()
+    return out
 
 
 def profile_run(args, X, Q, u, log):
