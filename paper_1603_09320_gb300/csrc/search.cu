@@ -111,6 +111,11 @@ struct SearchArgs {
     // two-pass scheduling: mode 0 = descent and beam per query in input order;
     // mode 1 = descent only, writing the layer-0 enter key and the upper-layer
     // counters of every query; mode 2 = beam only, queries taken in `order`
+    // grouped launch (several requests in one launch): per-query k (low 16
+    // bits) and ef (high 16 bits), and the first output slot of each query;
+    // null: k, efp and qi * k for every query
+    const uint32_t* q_kef;
+    const uint64_t* q_out;
     int mode;
     uint64_t* ep_keys;   // [n]
     uint32_t* up_cnt;    // [n][2]: distance evaluations, rows read on layers >= 1
@@ -515,6 +520,14 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
         if (qi >= a.n) break;
         if (a.mode == 2) qi = __ldg(a.order + qi);
         const float* qp = a.q + uint64_t(qi) * ix.d;
+        int kq = a.k, efq = a.efp;
+        uint64_t obase = uint64_t(qi) * uint64_t(a.k);
+        if (a.q_kef) {
+            const uint32_t v = __ldg(a.q_kef + qi);
+            kq = int(v & 0xffffu);
+            efq = max(kq, int(v >> 16));
+            obase = __ldg(a.q_out + qi);
+        }
         float qr[D::QF];
         D::load_q(qp, ix.d, qr, lane);
         if (a.rerank)
@@ -674,19 +687,19 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
                     __syncwarp();
                     n_eval += n;
                     n_eval0 += n;
-                    first_new = merge_batch(W, size, a.efp, ids, dst, n, ck, lbs, lane);
+                    first_new = merge_batch(W, size, efq, ids, dst, n, ck, lbs, lane);
                 }
                 scan = min(p + 1, first_new);
                 if (STOP && a.stop_period > 0) {
                     // the top-K of W changes exactly when its K-th key decreases
-                    const uint64_t kthk = size >= a.k ? (W[a.k - 1] >> 1) : ~0ull;
+                    const uint64_t kthk = size >= kq ? (W[kq - 1] >> 1) : ~0ull;
                     if (kthk < last_kth) {
                         last_kth = kthk;
                         stale = 0;
                     } else {
                         ++stale;
                     }
-                    if (size >= a.k && n_exp0 % uint32_t(a.stop_period) == 0) {
+                    if (size >= kq && n_exp0 % uint32_t(a.stop_period) == 0) {
                         const float d1n = fmaxf(d1, 1e-12f);
                         float f[kStopIn];
                         f[0] = log1pf(fmaxf(key_dist(W[0]) / d1n, 0.0f));
@@ -694,7 +707,7 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
                         f[2] = log1pf(float(n_eval0));
                         f[3] = log1pf(fmaxf(d1, 0.0f));
                         f[4] = log1pf(float(stale));
-                        f[5] = log1pf(fmaxf(key_dist(W[a.k - 1]) / d1n, 0.0f));
+                        f[5] = log1pf(fmaxf(key_dist(W[kq - 1]) / d1n, 0.0f));
                         const float logit = a.stop ? stop_logit(a.stop, f, reinterpret_cast<float*>(ck), lane) : 0.0f;
                         if (a.tr_count) {
                             if (n_checks < a.tr_max) {
@@ -732,7 +745,7 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
             __syncwarp();
             warp_sort(W, a.efcap, lane);
         }
-        for (int i = lane; i < a.k; i += 32) {
+        for (int i = lane; i < kq; i += 32) {
             uint32_t oid = kNone;
             float od = __int_as_float(0x7f800000);
             if (i < size) {
@@ -740,8 +753,8 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
                 oid = key_id(kk);
                 od = key_dist(kk);
             }
-            a.out_ids[uint64_t(qi) * a.k + i] = oid;
-            a.out_dists[uint64_t(qi) * a.k + i] = od;
+            a.out_ids[obase + i] = oid;
+            a.out_dists[obase + i] = od;
         }
         if (STOP && a.tr_count && lane == 0) a.tr_count[qi] = n_checks < a.tr_max ? n_checks : a.tr_max;
         if (a.stats && lane == 0) {
@@ -860,16 +873,18 @@ std::mutex g_attr_mu;
 }  // namespace
 
 int auto_visited_log2(int efp) {
-    // about 16 slots per beam entry: the evaluations of a layer-0 search are
-    // typically 10-30 x ef'; overflow only costs repeated evaluations
-    int l = ceil_log2(uint64_t(efp) * 16);
-    return l < 10 ? 10 : (l > 13 ? 13 : l);
+    // about 8-16 slots per beam entry, 1,024 to 4,096 slots: a layer-0 search
+    // evaluates some 10-30 x ef' elements, but a larger set costs occupancy
+    // and overflow only repeats evaluations
+    int l = ceil_log2(uint64_t(efp) * 8);
+    return l < 10 ? 10 : (l > 12 ? 12 : l);
 }
 
 hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n,
                                uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
                                uint32_t* work, const StopModel* stop, int mode, uint64_t* ep_keys,
-                               uint32_t* up_cnt, const uint32_t* order) {
+                               uint32_t* up_cnt, const uint32_t* order, const uint32_t* q_kef = nullptr,
+                               const uint64_t* q_out = nullptr) {
     const DevIndex& D = ix->dev;
     KernelChoice kc;
     if (!choose_kernel(D.storage, D.row_chunks, stop != nullptr && stop->period > 0, kc))
@@ -888,6 +903,8 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
     a.stats = stats;
     a.work = work;
     a.mode = mode;
+    a.q_kef = q_kef;
+    a.q_out = q_out;
     a.ep_keys = ep_keys;
     a.up_cnt = up_cnt;
     a.order = order;
@@ -933,6 +950,22 @@ hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const flo
     return launch_search_mode(ix, p, q, n, ids, dists, stats, s, work, stop, 0, nullptr, nullptr, nullptr);
 }
 
+// Grouped launch for the server: n queries of several requests on one index,
+// per-query k/ef packed in q_kef and output offsets in q_out (device arrays),
+// with max_k and max_ef sizing the per-warp state.
+hnsw_status launch_search_group(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n,
+                                int max_k, int max_ef, const uint32_t* q_kef, const uint64_t* q_out,
+                                uint32_t* ids, float* dists, cudaStream_t s, uint32_t* work,
+                                const StopModel* stop) {
+    hnsw_search_params pp = p;
+    pp.k = max_k;
+    pp.ef = max_ef;
+    cudaError_t e = cudaMemsetAsync(work, 0, 4, s);
+    if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("search group: ") + cudaGetErrorString(e));
+    return launch_search_mode(ix, pp, q, n, ids, dists, nullptr, s, work, stop, 0, nullptr, nullptr, nullptr,
+                              q_kef, q_out);
+}
+
 // A pair of work counters for one call (slots 2i and 2i+1 of the index's
 // ring): concurrent calls on one index use different counters.
 uint32_t take_work_slots(hnsw_index* ix) {
@@ -949,6 +982,27 @@ uint32_t resident_warps(const hnsw_index* ix) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return uint32_t(sms) * 28u;
+}
+
+// One launch over the queries of several requests of one index (the
+// server's grouped dispatch); device buffers; asynchronous on s.
+hnsw_status search_group(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n, int max_k,
+                         int max_ef, const uint32_t* q_kef, const uint64_t* q_out, uint32_t* ids, float* dists,
+                         cudaStream_t s) {
+    if (max_k < 1 || max_k > kMaxK || (max_ef > max_k ? max_ef : max_k) > kMaxEf)
+        return fail(HNSW_EINVAL, "search group: k or ef out of range");
+    if (p.rerank && !ix->dev.vec32) return fail(HNSW_EINVAL, "search group: rerank needs the fp32 copy");
+    StopModel sm{};
+    const StopModel* smp = nullptr;
+    if (p.stop_threshold > 0.0f && p.stop_threshold < 1.0f) {
+        if (!ix->d_stop) return fail(HNSW_EINVAL, "search group: stop_threshold in (0,1) needs a stop model");
+        sm.stop = ix->d_stop;
+        sm.logit_threshold = logf(p.stop_threshold / (1.0f - p.stop_threshold));
+        sm.period = p.stop_period > 0 ? p.stop_period : 8;
+        smp = &sm;
+    }
+    return launch_search_group(ix, p, q, n, max_k, max_ef, q_kef, q_out, ids, dists, s,
+                               ix->d_work + take_work_slots(ix), smp);
 }
 
 }  // namespace hnswgb

@@ -20,6 +20,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <algorithm>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -33,6 +34,11 @@
 #include "common.hpp"
 
 namespace hnswgb {
+// defined in search.cu: one launch over the queries of several requests
+hnsw_status search_group(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n, int max_k,
+                         int max_ef, const uint32_t* q_kef, const uint64_t* q_out, uint32_t* ids, float* dists,
+                         cudaStream_t s);
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -85,20 +91,21 @@ struct Request {
     uint64_t ticket = 0;
     hnsw_request r{};
     uint32_t d = 0;
-    uint64_t bytes = 0, off = 0;
-    int slot = -1;
+    uint64_t bytes = 0;   // device bytes of this request alone (admission check)
+    uint64_t q0 = 0, o0 = 0;  // first query / output slot inside its group
     Clock::time_point submitted, finished;
     hnsw_status status = HNSW_OK;
     std::string error;
-    std::atomic<bool> device_done{false};  // set by the stream callback
-    bool complete = false;     // results in the caller's buffers
+    bool complete = false;  // results in the caller's buffers
 };
 
 struct Slot {
     cudaStream_t stream = nullptr;
     void* pinned = nullptr;
     uint64_t pinned_bytes = 0;
-    Request* req = nullptr;
+    std::vector<Request*> group;           // requests of the launch on this slot
+    uint64_t off = 0, bytes = 0;           // their arena range
+    std::atomic<bool> device_done{false};  // set by the stream callback
 };
 
 }  // namespace
@@ -109,7 +116,7 @@ using namespace hnswgb;
 struct hnsw_server {
     int device = 0;
     std::vector<hnsw_index*> indexes;
-    std::vector<Slot> slots;
+    std::vector<std::unique_ptr<Slot>> slots;
     void* arena_base = nullptr;
     std::unique_ptr<Arena> arena;
     std::deque<Request*> pending;
@@ -125,119 +132,195 @@ struct hnsw_server {
 
 namespace {
 
-// Runs on the CUDA runtime's callback thread after a request's copies: it
+// Runs on the CUDA runtime's callback thread after a group's copies: it
 // takes no lock (the dispatcher may hold the server mutex across CUDA calls),
 // only publishes the flag and wakes the dispatcher, which also re-checks on a
 // short timeout in case this notification falls between its check and wait.
 void CUDART_CB on_device_done(void* p) {
-    auto* pair = static_cast<std::pair<hnsw_server*, Request*>*>(p);
+    auto* pair = static_cast<std::pair<hnsw_server*, Slot*>*>(p);
     pair->second->device_done.store(true, std::memory_order_release);
     pair->first->cv.notify_all();
     delete pair;
 }
 
-// Issues one admitted request on its slot's stream (called with mu held).
-void dispatch(hnsw_server* sv, Request* rq, int si) {
-    Slot& sl = sv->slots[si];
-    const hnsw_request& r = rq->r;
-    const uint64_t qb = uint64_t(r.n) * rq->d * 4, ob = uint64_t(r.n) * uint64_t(r.k) * 4;
-    char* dbase = static_cast<char*>(sv->arena_base) + rq->off;
-    float* dq = reinterpret_cast<float*>(dbase);
-    uint32_t* di = reinterpret_cast<uint32_t*>(dbase + up256(qb));
-    float* dd = reinterpret_cast<float*>(dbase + up256(qb) + up256(ob));
-    const uint64_t need_pinned = up256(qb) + 2 * up256(ob);
-    rq->slot = si;
-    sl.req = rq;
+// A group: requests admitted together into one launch (same index, same
+// options, same ef bucket).  Device and pinned layouts are identical:
+// [queries][ids][dists][k|ef per query][output offset per query], each
+// section 256-byte aligned.
+struct GroupLayout {
+    uint64_t nq = 0, nout = 0, q = 0, ids = 0, dists = 0, kef = 0, out = 0, total = 0;
+};
+
+GroupLayout layout_of(const std::vector<Request*>& g) {
+    GroupLayout L;
+    uint32_t d = g.front()->d;
+    for (Request* r : g) {
+        L.nq += uint64_t(r->r.n);
+        L.nout += uint64_t(r->r.n) * uint64_t(r->r.k);
+    }
+    L.q = 0;
+    L.ids = up256(L.nq * d * 4);
+    L.dists = L.ids + up256(L.nout * 4);
+    L.kef = L.dists + up256(L.nout * 4);
+    L.out = L.kef + up256(L.nq * 4);
+    L.total = L.out + up256(L.nq * 8);
+    return L;
+}
+
+bool compatible(const Request* a, const Request* b) {
+    auto bucket = [](const hnsw_request& r) {
+        int e = r.ef > r.k ? r.ef : r.k, b = 32;
+        while (b < e) b <<= 1;
+        return b;
+    };
+    return a->r.index == b->r.index && a->r.rerank == b->r.rerank && a->r.stop_threshold == b->r.stop_threshold &&
+           a->r.stop_period == b->r.stop_period && bucket(a->r) == bucket(b->r);
+}
+
+// Issues one admitted group on its slot's stream (called with mu held).
+void dispatch(hnsw_server* sv, std::vector<Request*>& g, uint64_t off, int si) {
+    Slot& sl = *sv->slots[si];
+    const GroupLayout L = layout_of(g);
+    const uint32_t d = g.front()->d;
+    char* db = static_cast<char*>(sv->arena_base) + off;
+    sl.group = g;
+    sl.off = off;
+    sl.bytes = L.total;
     cudaError_t e = cudaSuccess;
-    if (sl.pinned_bytes < need_pinned) {
+    if (sl.pinned_bytes < L.total) {
         if (sl.pinned) cudaFreeHost(sl.pinned);
         sl.pinned = nullptr;
         sl.pinned_bytes = 0;
-        e = cudaMallocHost(&sl.pinned, need_pinned);
-        if (e == cudaSuccess) sl.pinned_bytes = need_pinned;
+        e = cudaMallocHost(&sl.pinned, L.total);
+        if (e == cudaSuccess) sl.pinned_bytes = L.total;
     }
     hnsw_status st = HNSW_OK;
     if (e != cudaSuccess) {
         st = fail(HNSW_ENOMEM, "server: pinned staging");
     } else {
         char* hp = static_cast<char*>(sl.pinned);
-        std::memcpy(hp, r.queries, qb);
-        e = cudaMemcpyAsync(dq, hp, qb, cudaMemcpyHostToDevice, sl.stream);
+        uint32_t* kef = reinterpret_cast<uint32_t*>(hp + L.kef);
+        uint64_t* oo = reinterpret_cast<uint64_t*>(hp + L.out);
+        uint64_t qi = 0, ob = 0;
+        int max_k = 1, max_ef = 1;
+        for (Request* r : g) {
+            std::memcpy(hp + L.q + qi * d * 4, r->r.queries, uint64_t(r->r.n) * d * 4);
+            r->q0 = qi;
+            r->o0 = ob;
+            for (int64_t j = 0; j < r->r.n; ++j) {
+                kef[qi + j] = uint32_t(r->r.k) | (uint32_t(r->r.ef) << 16);
+                oo[qi + j] = ob + uint64_t(j) * uint64_t(r->r.k);
+            }
+            qi += uint64_t(r->r.n);
+            ob += uint64_t(r->r.n) * uint64_t(r->r.k);
+            max_k = r->r.k > max_k ? r->r.k : max_k;
+            max_ef = r->r.ef > max_ef ? r->r.ef : max_ef;
+        }
+        e = cudaMemcpyAsync(db + L.q, hp + L.q, L.ids - L.q, cudaMemcpyHostToDevice, sl.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(db + L.kef, hp + L.kef, L.total - L.kef, cudaMemcpyHostToDevice, sl.stream);
         if (e == cudaSuccess) {
+            const hnsw_request& r0 = g.front()->r;
             hnsw_search_params p{};
-            p.k = r.k;
-            p.ef = r.ef;
-            p.rerank = r.rerank;
-            p.stop_threshold = r.stop_threshold;
-            p.stop_period = r.stop_period;
-            st = hnsw_search_ex(sv->indexes[r.index], &p, dq, r.n, di, dd, nullptr, sl.stream);
+            p.k = max_k;
+            p.ef = max_ef;
+            p.rerank = r0.rerank;
+            p.stop_threshold = r0.stop_threshold;
+            p.stop_period = r0.stop_period;
+            st = search_group(sv->indexes[r0.index], p, reinterpret_cast<const float*>(db + L.q), uint32_t(L.nq),
+                              max_k, max_ef, reinterpret_cast<const uint32_t*>(db + L.kef),
+                              reinterpret_cast<const uint64_t*>(db + L.out), reinterpret_cast<uint32_t*>(db + L.ids),
+                              reinterpret_cast<float*>(db + L.dists), sl.stream);
         } else {
             st = fail(HNSW_ECUDA, std::string("server: H2D: ") + cudaGetErrorString(e));
         }
         if (st == HNSW_OK) {
-            e = cudaMemcpyAsync(hp + up256(qb), di, ob, cudaMemcpyDeviceToHost, sl.stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hp + up256(qb) + up256(ob), dd, ob, cudaMemcpyDeviceToHost, sl.stream);
-            if (e == cudaSuccess)
-                e = cudaLaunchHostFunc(sl.stream, on_device_done, new std::pair<hnsw_server*, Request*>(sv, rq));
+            e = cudaMemcpyAsync(hp + L.ids, db + L.ids, L.kef - L.ids, cudaMemcpyDeviceToHost, sl.stream);
+            if (e == cudaSuccess) e = cudaLaunchHostFunc(sl.stream, on_device_done, new std::pair<hnsw_server*, Slot*>(sv, &sl));
             if (e != cudaSuccess) st = fail(HNSW_ECUDA, std::string("server: ") + cudaGetErrorString(e));
         }
     }
-    if (st != HNSW_OK) {  // nothing more runs for this request on the device
-        rq->status = st;
-        rq->error = hnsw_last_error();
+    if (st != HNSW_OK) {  // nothing more runs for this group on the device
+        const std::string err = hnsw_last_error();
+        for (Request* r : g) {
+            r->status = st;
+            r->error = err;
+        }
         cudaStreamSynchronize(sl.stream);
-        rq->device_done.store(true, std::memory_order_release);
+        sl.device_done.store(true, std::memory_order_release);
     }
 }
 
 // Copies results out and releases the slot and arena range (mu held).
-void complete(hnsw_server* sv, Request* rq) {
-    Slot& sl = sv->slots[rq->slot];
-    const hnsw_request& r = rq->r;
-    if (rq->status == HNSW_OK) {
-        const uint64_t qb = uint64_t(r.n) * rq->d * 4, ob = uint64_t(r.n) * uint64_t(r.k) * 4;
-        const char* hp = static_cast<const char*>(sl.pinned);
-        std::memcpy(r.out_ids, hp + up256(qb), ob);
-        std::memcpy(r.out_dists, hp + up256(qb) + up256(ob), ob);
-        sv->stats.completed++;
-    } else {
-        sv->stats.failed++;
+void complete(hnsw_server* sv, Slot& sl) {
+    const GroupLayout L = layout_of(sl.group);
+    const char* hp = static_cast<const char*>(sl.pinned);
+    const auto now = Clock::now();
+    for (Request* r : sl.group) {
+        if (r->status == HNSW_OK) {
+            const uint64_t ob = uint64_t(r->r.n) * uint64_t(r->r.k) * 4;
+            std::memcpy(r->r.out_ids, hp + L.ids + r->o0 * 4, ob);
+            std::memcpy(r->r.out_dists, hp + L.dists + r->o0 * 4, ob);
+            sv->stats.completed++;
+        } else {
+            sv->stats.failed++;
+        }
+        r->finished = now;
+        r->complete = true;
+        sv->stats.in_flight--;
     }
-    sv->arena->release(rq->off, rq->bytes);
-    sl.req = nullptr;
-    rq->finished = Clock::now();
-    rq->complete = true;
-    sv->stats.in_flight--;
+    sv->arena->release(sl.off, sl.bytes);
+    sl.group.clear();
+    sl.device_done.store(false, std::memory_order_relaxed);
 }
+
+constexpr uint64_t kMaxGroupQueries = 8192;
+constexpr int kGroupWindow = 512;
 
 void worker_loop(hnsw_server* sv) {
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
         bool progress = false;
-        for (auto& sl : sv->slots)
-            if (sl.req && sl.req->device_done.load(std::memory_order_acquire)) {
-                complete(sv, sl.req);
+        for (auto& slp : sv->slots)
+            if (!slp->group.empty() && slp->device_done.load(std::memory_order_acquire)) {
+                complete(sv, *slp);
                 progress = true;
             }
         if (progress) sv->done_cv.notify_all();
-        // admit from the head of the queue while a slot and arena space are free
+        // admit groups from the head of the queue while a slot and arena space are free
         while (!sv->pending.empty()) {
             int si = -1;
             for (size_t i = 0; i < sv->slots.size(); ++i)
-                if (!sv->slots[i].req) {
+                if (sv->slots[i]->group.empty()) {
                     si = int(i);
                     break;
                 }
             if (si < 0) break;
-            Request* rq = sv->pending.front();
+            // the head, plus compatible requests further back (up to a window)
+            std::vector<Request*> g{sv->pending.front()};
+            uint64_t nq = uint64_t(g[0]->r.n);
+            int scanned = 0;
+            for (auto it = std::next(sv->pending.begin()); it != sv->pending.end() && scanned < kGroupWindow;
+                 ++it, ++scanned)
+                if (compatible(*it, g[0]) && nq + uint64_t((*it)->r.n) <= kMaxGroupQueries) {
+                    g.push_back(*it);
+                    nq += uint64_t((*it)->r.n);
+                }
             uint64_t off = 0;
-            if (!sv->arena->alloc(rq->bytes, off)) break;  // wait for memory to free up
-            rq->off = off;
-            sv->pending.pop_front();
-            sv->stats.queued--;
-            sv->stats.in_flight++;
-            dispatch(sv, rq, si);
+            bool fits = false;
+            for (;;) {
+                if (sv->arena->alloc(layout_of(g).total, off)) {
+                    fits = true;
+                    break;
+                }
+                if (g.size() == 1) break;
+                g.pop_back();  // a smaller group
+            }
+            if (!fits) break;  // the head does not fit now: wait for completions
+            for (Request* r : g) sv->pending.erase(std::find(sv->pending.begin(), sv->pending.end(), r));
+            sv->stats.queued -= g.size();
+            sv->stats.in_flight += g.size();
+            dispatch(sv, g, off, si);
         }
         sv->stats.bytes_in_use = sv->arena->used();
         if (sv->stopping && sv->pending.empty() && sv->stats.in_flight == 0) break;
@@ -270,11 +353,11 @@ extern "C" hnsw_status hnsw_server_create(const hnsw_server_params* p, hnsw_serv
     }
     sv->arena.reset(new Arena(budget));
     sv->stats.budget = budget;
-    sv->slots.resize(size_t(p->n_slots));
+    for (int i = 0; i < p->n_slots; ++i) sv->slots.emplace_back(new Slot());
     for (auto& sl : sv->slots)
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess) {
             for (auto& s2 : sv->slots)
-                if (s2.stream) cudaStreamDestroy(s2.stream);
+                if (s2->stream) cudaStreamDestroy(s2->stream);
             cudaFree(sv->arena_base);
             return fail(HNSW_ECUDA, "hnsw_server_create: stream");
         }
@@ -307,7 +390,7 @@ extern "C" hnsw_status hnsw_server_submit(hnsw_server* sv, const hnsw_request* r
     if (r->n < 1 || r->k < 1 || r->ef < 1 || !r->queries || !r->out_ids || !r->out_dists)
         return fail(HNSW_EINVAL, "hnsw_server_submit: bad request");
     const uint64_t qb = uint64_t(r->n) * rq->d * 4, ob = uint64_t(r->n) * uint64_t(r->k) * 4;
-    rq->bytes = up256(qb) + 2 * up256(ob);
+    rq->bytes = up256(qb) + 2 * up256(ob) + up256(uint64_t(r->n) * 4) + up256(uint64_t(r->n) * 8);
     if (rq->bytes > sv->arena->cap())
         return fail(HNSW_EINVAL, "hnsw_server_submit: request larger than the memory budget");
     rq->submitted = Clock::now();
@@ -371,11 +454,11 @@ extern "C" hnsw_status hnsw_server_destroy(hnsw_server* sv) {
     sv->cv.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
     for (auto& sl : sv->slots) {
-        if (sl.stream) {
-            cudaStreamSynchronize(sl.stream);
-            cudaStreamDestroy(sl.stream);
+        if (sl->stream) {
+            cudaStreamSynchronize(sl->stream);
+            cudaStreamDestroy(sl->stream);
         }
-        if (sl.pinned) cudaFreeHost(sl.pinned);
+        if (sl->pinned) cudaFreeHost(sl->pinned);
     }
     cudaFree(sv->arena_base);
     delete sv;
