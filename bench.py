@@ -37,6 +37,35 @@ METRIC = "QPS at recall@10≥0.95, 1M×128, chosen vs plain GPU form; % of HBM-g
 EF_SWEEP = [10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 400]
 
 
+def max_over_ranks(ms: float, pg) -> float:
+    """The step time of the slowest rank (gloo all-reduce; pg None: one rank)."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_qps(n_per_rank: int, world: int, ms: float) -> float:
+    """Queries per second of the whole job: every rank searches its own batch
+    of n_per_rank queries (replicas, weak scaling) in the slowest rank's time."""
+    return n_per_rank * world / (ms / 1e3)
+
+
+def shared_graph(args, X, u, log, rank, pg):
+    """Rank 0 builds (or finds) the cached graph; the others load it after a
+    barrier, so every replica searches the same graph."""
+    blob, build_s = (None, None)
+    if rank == 0:
+        blob, build_s = graph_blob(args, X, u, log)
+    if pg is not None:
+        pg.barrier()
+    if rank != 0:
+        blob, _ = graph_blob(args, X, u, log)
+    return blob, build_s
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,13 +433,7 @@ def main():
     X, Q, u = workload(args)
     if args.profile_form:
         return profile_run(args, X, Q, u, log)
-    build_s = None
-    if rank == 0:
-        blob, build_s = graph_blob(args, X, u, log)
-    if pg:
-        pg.barrier()
-    if rank != 0:
-        blob, _ = graph_blob(args, X, u, log)
+    blob, build_s = shared_graph(args, X, u, log, rank, pg)
     gt = ground_truth(X, Q, args.k, torch.device("cuda", local))
     forms, indexes, bufs = run_forms(args, blob, X, Q, gt, log)
     ok = {n: f for n, f in forms.items() if f["setting"] is not None}
@@ -436,13 +459,9 @@ def main():
     if pg:
         pg.barrier()
     clk = clocks.stop()
-    ms = statistics.mean(times)
-    if pg:
-        t = torch.tensor([ms], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(times), pg)
     n = Q.shape[0]
-    value = n * world / (ms / 1e3)
+    value = whole_job_qps(n, world, ms)
     # plain form beside it
     sp = ok["f32"]["setting"]
     tp, stats_p = time_form(args, indexes["f32"], sp, bufs, args.steps, args.warmup, flush)
