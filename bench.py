@@ -540,8 +540,6 @@ def serving_bench(args, log):
     configurations: plain fp32, and bf16 storage with the exact fp32 rerank.
     Reports queries/s, requests/s, p50/p99 latency and recall@10 (requests
     with k >= 10) against exact k-NN."""
-    import threading
-    import torch
     from paper_1603_09320_gb300 import build as B
     from paper_1603_09320_gb300 import graphs, hnsw, synth
     B.build()
@@ -570,56 +568,39 @@ def serving_bench(args, log):
                                   "log-uniform, k in {1,10,100}, ef uniform [k,512], index 50/50",
                       "requests": n_req, "queries": int(sum(p[2] for p in plan)),
                       "build_seconds": {k2: v[3] for k2, v in sets.items()}}, "variants": {}}
+    rates = sorted(set([args.serving_rate / 4, args.serving_rate / 2, args.serving_rate]))
     for variant, (storage, keep, rerank) in {"plain_f32": ("f32", False, False),
                                              "bf16_rerank": ("bf16", True, True)}.items():
         ixs = {name: hnsw.Index(sets[name][0], storage, keep_fp32=keep) for name in sets}
-        sv = hnsw.Server(n_slots=16)
-        ids_ = {name: sv.add_index(ix) for name, ix in ixs.items()}
-        tickets = [None] * n_req
-        sub_t = np.zeros(n_req)
-        t0 = time.perf_counter()
-
-        def producer():
-            for i, (name, s0, n, k, ef) in enumerate(plan):
-                while time.perf_counter() - t0 < arrivals[i]:
-                    pass
-                sub_t[i] = time.perf_counter() - t0
-                tickets[i] = sv.submit(ids_[name], sets[name][1][s0:s0 + n], k, ef, rerank=rerank)
-
-        th = threading.Thread(target=producer)
-        th.start()
-        lat = np.zeros(n_req)
-        results = [None] * n_req
-        for i in range(n_req):
-            while tickets[i] is None:
-                time.sleep(0.0001)
-            ids, ds, ms = sv.wait(tickets[i], timeout_ms=120_000)
-            lat[i] = ms
-            results[i] = ids
-        th.join()
-        # the span from the first arrival to the last completion, from the
-        # server's own submit-to-completion times
-        wall = float(np.max(sub_t + lat / 1e3))
-        lag = float(np.max(sub_t - arrivals))
-        hits = total = 0
-        for i, (name, s0, n, k, ef) in enumerate(plan):
-            if k >= 10:
-                got = np.sort(results[i][:, :10].astype(np.int64), axis=1)
-                gt = np.sort(sets[name][2][s0:s0 + n], axis=1)
-                hits += int((got[:, :, None] == gt[:, None, :]).any(axis=2).sum())
-                total += n * 10
-        st = sv.stats()
-        sv.close()
+        out["variants"][variant] = {}
+        for rate in rates:
+            m = int(rate * args.serving_seconds)
+            arr = arrivals[:m] * (args.serving_rate / rate)  # the same requests, spread out
+            sv = hnsw.Server(n_slots=16)
+            ids_ = {name: sv.add_index(ix) for name, ix in ixs.items()}
+            reqs = [(ids_[name], sets[name][1][s0:s0 + n], k, ef, rerank) for (name, s0, n, k, ef) in plan[:m]]
+            res, lat, sub = sv.replay(reqs, arr)
+            st = sv.stats()
+            sv.close()
+            wall = float(np.max(sub + lat / 1e3))
+            hits = total = 0
+            for i, (name, s0, n, k, ef) in enumerate(plan[:m]):
+                if k >= 10:
+                    got = np.sort(res[i][0][:, :10].astype(np.int64), axis=1)
+                    gt = np.sort(sets[name][2][s0:s0 + n], axis=1)
+                    hits += int((got[:, :, None] == gt[:, None, :]).any(axis=2).sum())
+                    total += n * 10
+            qn = int(sum(p[2] for p in plan[:m]))
+            out["variants"][variant][f"{rate:.0f}_req_per_s"] = {
+                "offered_queries_per_s": round(qn / args.serving_seconds, 1),
+                "served_queries_per_s": round(qn / wall, 1), "requests": m,
+                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "mean_ms": round(float(lat.mean()), 3), "wall_s": round(wall, 3),
+                "recall_at_10": round(hits / max(total, 1), 5), "failed": st["failed"],
+                "max_submit_lag_ms": round(float(np.max(sub - arr)) * 1e3, 3)}
+            log(f"serving {variant} {rate:.0f}/s: {out['variants'][variant][f'{rate:.0f}_req_per_s']}")
         for ix in ixs.values():
             ix.close()
-        qn = out["config"]["queries"]
-        out["variants"][variant] = {"queries_per_s": round(qn / wall, 1), "requests_per_s": round(n_req / wall, 1),
-                                    "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                                    "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                                    "mean_ms": round(float(lat.mean()), 3), "wall_s": round(wall, 3),
-                                    "recall_at_10": round(hits / max(total, 1), 5), "failed": st["failed"],
-                                    "max_submit_lag_ms": round(lag * 1e3, 3)}
-        log(f"serving {variant}: {out['variants'][variant]}")
     print(json.dumps(out), flush=True)
 
 

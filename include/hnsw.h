@@ -315,6 +315,14 @@ hnsw_status hnsw_server_get_stats(hnsw_server* server, hnsw_server_stats* out);
  * arena. */
 hnsw_status hnsw_server_destroy(hnsw_server* server);
 
+/* Replays a request trace: submits reqs[i] at arrival_s[i] seconds after the
+ * call starts (busy-waiting between arrivals), then waits for all of them
+ * (timeout_ms per request) and writes each submit-to-completion latency to
+ * latency_ms[i] and, when submit_s is not NULL, the actual submit time.
+ * Returns the first error of a request, if any. */
+hnsw_status hnsw_server_replay(hnsw_server* server, const hnsw_request* reqs, const double* arrival_s, int64_t n,
+                               int32_t timeout_ms, double* latency_ms, double* submit_s);
+
 /* Thread-local message describing the last failure of this thread. */
 const char* hnsw_last_error(void);
 

@@ -520,13 +520,12 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
         if (qi >= a.n) break;
         if (a.mode == 2) qi = __ldg(a.order + qi);
         const float* qp = a.q + uint64_t(qi) * ix.d;
-        int kq = a.k, efq = a.efp;
-        uint64_t obase = uint64_t(qi) * uint64_t(a.k);
+        // per-query k and ef of a grouped launch (k is reread where needed so
+        // that only ef stays live through the search)
+        int efq = a.efp;
         if (a.q_kef) {
             const uint32_t v = __ldg(a.q_kef + qi);
-            kq = int(v & 0xffffu);
-            efq = max(kq, int(v >> 16));
-            obase = __ldg(a.q_out + qi);
+            efq = max(int(v & 0xffffu), int(v >> 16));
         }
         float qr[D::QF];
         D::load_q(qp, ix.d, qr, lane);
@@ -691,6 +690,7 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
                 }
                 scan = min(p + 1, first_new);
                 if (STOP && a.stop_period > 0) {
+                    const int kq = a.q_kef ? int(__ldg(a.q_kef + qi) & 0xffffu) : a.k;
                     // the top-K of W changes exactly when its K-th key decreases
                     const uint64_t kthk = size >= kq ? (W[kq - 1] >> 1) : ~0ull;
                     if (kthk < last_kth) {
@@ -745,6 +745,8 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
             __syncwarp();
             warp_sort(W, a.efcap, lane);
         }
+        const int kq = a.q_kef ? int(__ldg(a.q_kef + qi) & 0xffffu) : a.k;
+        const uint64_t obase = a.q_kef ? __ldg(a.q_out + qi) : uint64_t(qi) * uint64_t(a.k);
         for (int i = lane; i < kq; i += 32) {
             uint32_t oid = kNone;
             float od = __int_as_float(0x7f800000);

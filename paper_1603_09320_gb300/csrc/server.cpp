@@ -464,3 +464,27 @@ extern "C" hnsw_status hnsw_server_destroy(hnsw_server* sv) {
     delete sv;
     return HNSW_OK;
 }
+
+extern "C" hnsw_status hnsw_server_replay(hnsw_server* sv, const hnsw_request* reqs, const double* arrival_s,
+                                          int64_t n, int32_t timeout_ms, double* latency_ms, double* submit_s) {
+    if (!sv || (n > 0 && (!reqs || !arrival_s || !latency_ms))) return fail(HNSW_EINVAL, "hnsw_server_replay: null argument");
+    std::vector<uint64_t> tickets(size_t(n > 0 ? n : 0));
+    const auto t0 = Clock::now();
+    for (int64_t i = 0; i < n; ++i) {
+        const auto due = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(arrival_s[i]));
+        while (Clock::now() < due) {
+        }
+        if (submit_s) submit_s[i] = std::chrono::duration<double>(Clock::now() - t0).count();
+        const hnsw_status st = hnsw_server_submit(sv, &reqs[i], &tickets[size_t(i)]);
+        if (st != HNSW_OK) {
+            for (int64_t j = 0; j < i; ++j) hnsw_server_wait(sv, tickets[size_t(j)], -1, nullptr);
+            return st;
+        }
+    }
+    hnsw_status first = HNSW_OK;
+    for (int64_t i = 0; i < n; ++i) {
+        const hnsw_status st = hnsw_server_wait(sv, tickets[size_t(i)], timeout_ms, &latency_ms[i]);
+        if (st != HNSW_OK && first == HNSW_OK) first = st;
+    }
+    return first;
+}

@@ -111,6 +111,7 @@ def lib():
             "hnsw_server_wait": (i32, [vp, u64, i32, C.POINTER(C.c_double)]),
             "hnsw_server_get_stats": (i32, [vp, C.POINTER(ServerStats)]),
             "hnsw_server_destroy": (i32, [vp]),
+            "hnsw_server_replay": (i32, [vp, C.POINTER(Request), vp, i64, i32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -319,6 +320,24 @@ class Server:
         _check(lib().hnsw_server_submit(self.h, C.byref(r), C.byref(t)))
         self._live[int(t.value)] = (q, ids, ds)
         return int(t.value)
+
+    def replay(self, plan, arrival_s, timeout_ms: int = 600_000):
+        """Native trace replay: plan is a list of (index_id, queries, k, ef,
+        rerank); returns (per-request (ids, dists), latency_ms, submit_s)."""
+        n = len(plan)
+        reqs = (Request * n)()
+        keep = []
+        for i, (idx, q, k, ef, rr) in enumerate(plan):
+            q = np.ascontiguousarray(q, dtype=np.float32)
+            ids = np.empty((q.shape[0], k), dtype=np.uint32)
+            ds = np.empty((q.shape[0], k), dtype=np.float32)
+            reqs[i] = Request(idx, q.shape[0], k, ef, int(rr), 2.0, 0, q.ctypes.data, ids.ctypes.data, ds.ctypes.data)
+            keep.append((q, ids, ds))
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.zeros(n, dtype=np.float64)
+        sub = np.zeros(n, dtype=np.float64)
+        _check(lib().hnsw_server_replay(self.h, reqs, arr.ctypes.data, n, timeout_ms, lat.ctypes.data, sub.ctypes.data))
+        return [(k2[1], k2[2]) for k2 in keep], lat, sub
 
     def poll(self, ticket: int) -> bool:
         d = C.c_int32()

@@ -88,3 +88,20 @@ def test_request_larger_than_budget_is_rejected(setup):
     ai, _ = ixs[1].search(Qs[1][:10], 10, 32)
     np.testing.assert_array_equal(ids, ai)
     sv.close()
+
+
+def test_replay_equals_alone(setup):
+    hnsw, ixs, Qs = setup
+    rng = np.random.default_rng(11)
+    reqs = _requests(rng, Qs, 60)
+    sv = hnsw.Server(n_slots=4)
+    ids_ = [sv.add_index(ix) for ix in ixs]
+    plan = [(ids_[w], q, k, ef, rr) for (w, q, k, ef, rr) in reqs]
+    arrivals = np.cumsum(rng.exponential(1e-4, size=len(plan)))
+    res, lat, sub = sv.replay(plan, arrivals)
+    sv.close()
+    assert (lat > 0).all() and (sub >= arrivals - 1e-6).all()
+    for (w, q, k, ef, rr), (ids, ds) in zip(reqs, res):
+        ai, ad = ixs[w].search(q, k, ef, rerank=rr)
+        np.testing.assert_array_equal(ids, ai)
+        np.testing.assert_array_equal(ds, ad)
