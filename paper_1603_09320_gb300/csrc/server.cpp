@@ -106,6 +106,7 @@ struct Slot {
     std::vector<Request*> group;           // requests of the launch on this slot
     uint64_t off = 0, bytes = 0;           // their arena range
     std::atomic<bool> device_done{false};  // set by the stream callback
+    bool releasing = false;                // results being copied out
 };
 
 }  // namespace
@@ -177,15 +178,15 @@ bool compatible(const Request* a, const Request* b) {
            a->r.stop_period == b->r.stop_period && bucket(a->r) == bucket(b->r);
 }
 
-// Issues one admitted group on its slot's stream (called with mu held).
-void dispatch(hnsw_server* sv, std::vector<Request*>& g, uint64_t off, int si) {
-    Slot& sl = *sv->slots[si];
+// Issues one admitted group on its slot's stream.  Called WITHOUT the server
+// mutex: it touches only its slot (reserved by the caller), the group's arena
+// range and the group's requests, none of which another thread uses until the
+// slot's device_done flag is set.
+void dispatch(hnsw_server* sv, hnsw_index* ix, Slot& sl) {
+    std::vector<Request*>& g = sl.group;
     const GroupLayout L = layout_of(g);
     const uint32_t d = g.front()->d;
-    char* db = static_cast<char*>(sv->arena_base) + off;
-    sl.group = g;
-    sl.off = off;
-    sl.bytes = L.total;
+    char* db = static_cast<char*>(sv->arena_base) + sl.off;
     cudaError_t e = cudaSuccess;
     if (sl.pinned_bytes < L.total) {
         if (sl.pinned) cudaFreeHost(sl.pinned);
@@ -226,7 +227,7 @@ void dispatch(hnsw_server* sv, std::vector<Request*>& g, uint64_t off, int si) {
             p.rerank = r0.rerank;
             p.stop_threshold = r0.stop_threshold;
             p.stop_period = r0.stop_period;
-            st = search_group(sv->indexes[r0.index], p, reinterpret_cast<const float*>(db + L.q), uint32_t(L.nq),
+            st = search_group(ix, p, reinterpret_cast<const float*>(db + L.q), uint32_t(L.nq),
                               max_k, max_ef, reinterpret_cast<const uint32_t*>(db + L.kef),
                               reinterpret_cast<const uint64_t*>(db + L.out), reinterpret_cast<uint32_t*>(db + L.ids),
                               reinterpret_cast<float*>(db + L.dists), sl.stream);
@@ -250,20 +251,27 @@ void dispatch(hnsw_server* sv, std::vector<Request*>& g, uint64_t off, int si) {
     }
 }
 
-// Copies results out and releases the slot and arena range (mu held).
-void complete(hnsw_server* sv, Slot& sl) {
+// Copies a finished group's results into the callers' buffers (no mutex:
+// the slot and its requests belong to the dispatcher until released).
+void copy_out(Slot& sl) {
     const GroupLayout L = layout_of(sl.group);
     const char* hp = static_cast<const char*>(sl.pinned);
-    const auto now = Clock::now();
-    for (Request* r : sl.group) {
+    for (Request* r : sl.group)
         if (r->status == HNSW_OK) {
             const uint64_t ob = uint64_t(r->r.n) * uint64_t(r->r.k) * 4;
             std::memcpy(r->r.out_ids, hp + L.ids + r->o0 * 4, ob);
             std::memcpy(r->r.out_dists, hp + L.dists + r->o0 * 4, ob);
-            sv->stats.completed++;
-        } else {
-            sv->stats.failed++;
         }
+}
+
+// Marks the group complete and releases the slot and arena range (mu held).
+void release(hnsw_server* sv, Slot& sl) {
+    const auto now = Clock::now();
+    for (Request* r : sl.group) {
+        if (r->status == HNSW_OK)
+            sv->stats.completed++;
+        else
+            sv->stats.failed++;
         r->finished = now;
         r->complete = true;
         sv->stats.in_flight--;
@@ -280,13 +288,22 @@ void worker_loop(hnsw_server* sv) {
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
-        bool progress = false;
+        std::vector<Slot*> done;
         for (auto& slp : sv->slots)
-            if (!slp->group.empty() && slp->device_done.load(std::memory_order_acquire)) {
-                complete(sv, *slp);
-                progress = true;
+            if (!slp->group.empty() && !slp->releasing && slp->device_done.load(std::memory_order_acquire)) {
+                slp->releasing = true;
+                done.push_back(slp.get());
             }
-        if (progress) sv->done_cv.notify_all();
+        if (!done.empty()) {
+            lk.unlock();
+            for (Slot* sl : done) copy_out(*sl);
+            lk.lock();
+            for (Slot* sl : done) {
+                release(sv, *sl);
+                sl->releasing = false;
+            }
+            sv->done_cv.notify_all();
+        }
         // admit groups from the head of the queue while a slot and arena space are free
         while (!sv->pending.empty()) {
             int si = -1;
@@ -320,7 +337,14 @@ void worker_loop(hnsw_server* sv) {
             for (Request* r : g) sv->pending.erase(std::find(sv->pending.begin(), sv->pending.end(), r));
             sv->stats.queued -= g.size();
             sv->stats.in_flight += g.size();
-            dispatch(sv, g, off, si);
+            Slot& sl = *sv->slots[si];
+            sl.group = g;  // reserves the slot
+            sl.off = off;
+            sl.bytes = layout_of(g).total;
+            hnsw_index* ix = sv->indexes[g.front()->r.index];
+            lk.unlock();
+            dispatch(sv, ix, sl);
+            lk.lock();
         }
         sv->stats.bytes_in_use = sv->arena->used();
         if (sv->stopping && sv->pending.empty() && sv->stats.in_flight == 0) break;
