@@ -473,6 +473,68 @@ __device__ int merge_batch(uint64_t* W, int& size, int efp, const uint32_t* ids,
     return lbmin;
 }
 
+// merge_batch for a list of at most 64 entries and at most 32 new
+// neighbours: W is read into registers (entries lane and lane + 32), each
+// surviving neighbour's position and duplicate test come from two ballots,
+// and every entry is written once to its new position.  Same result as
+// merge_batch.
+__device__ int merge_small(uint64_t* W, int& size, int efp, const uint32_t* ids, const float* dst, int n,
+                           int lane) {
+    const uint64_t w0 = lane < size ? W[lane] : ~0ull;
+    const uint64_t w1 = lane + 32 < size ? W[lane + 32] : ~0ull;
+    const uint64_t a0 = w0 >> 1, a1 = w1 >> 1;  // keys without the expanded bit
+    const bool full = size >= efp;
+    uint64_t wlast = 0;
+    if (size > 0) {
+        const int t = size - 1;
+        wlast = __shfl_sync(kFull, t >= 32 ? a1 : a0, t & 31);
+    }
+    uint64_t k = 0;
+    bool ok = false;
+    if (lane < n) {
+        k = mkkey(dst[lane], ids[lane]);
+        ok = !(full && (k >> 1) > wlast);
+    }
+    const uint32_t surv = __ballot_sync(kFull, ok);
+    if (surv == 0) return INT_MAX;
+    const uint64_t k1 = k >> 1;
+    int cnt0 = 0, cnt1 = 0;  // new entries placed before my W entries
+    int mylb = 0, myrank = 0;
+    bool mine_dup = false;
+    int m = 0;
+    for (uint32_t bits = surv; bits; bits &= bits - 1) {
+        const int sl = __ffs(bits) - 1;
+        const uint64_t ks = __shfl_sync(kFull, k1, sl);
+        const bool dup = __any_sync(kFull, a0 == ks || a1 == ks);  // already in W
+        if (dup) {
+            if (lane == sl) mine_dup = true;
+            continue;
+        }
+        ++m;
+        cnt0 += a0 != (~0ull >> 1) && ks < a0;
+        cnt1 += a1 != (~0ull >> 1) && ks < a1;
+        const int lb = __popc(__ballot_sync(kFull, lane < size && a0 < ks)) +
+                       __popc(__ballot_sync(kFull, lane + 32 < size && a1 < ks));
+        if (lane == sl) mylb = lb;
+        if (ok && ks < k1) ++myrank;
+    }
+    __syncwarp();
+    if (m == 0) return INT_MAX;
+    if (lane < size && lane + cnt0 < efp) W[lane + cnt0] = w0;
+    if (lane + 32 < size && lane + 32 + cnt1 < efp) W[lane + 32 + cnt1] = w1;
+    int pos = INT_MAX;
+    if (ok && !mine_dup) {
+        pos = mylb + myrank;
+        if (pos < efp)
+            W[pos] = k;
+        else
+            pos = INT_MAX;
+    }
+    size = min(efp, size + m);
+    __syncwarp();
+    return int(__reduce_min_sync(kFull, uint32_t(pos)));
+}
+
 // warp-wide bitonic sort of n (power of two) keys in shared memory
 __device__ void warp_sort(uint64_t* a, int n, int lane) {
     for (int kk = 2; kk <= n; kk <<= 1)
@@ -686,7 +748,9 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
                     __syncwarp();
                     n_eval += n;
                     n_eval0 += n;
-                    first_new = merge_batch(W, size, efq, ids, dst, n, ck, lbs, lane);
+                    first_new = (a.efcap <= 64 && n <= 32)
+                                    ? merge_small(W, size, efq, ids, dst, n, lane)
+                                    : merge_batch(W, size, efq, ids, dst, n, ck, lbs, lane);
                 }
                 scan = min(p + 1, first_new);
                 if (STOP && a.stop_period > 0) {
