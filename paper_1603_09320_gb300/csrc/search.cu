@@ -559,8 +559,16 @@ __device__ __forceinline__ uint32_t ix_row32(const SearchArgs& a) { return a.ix.
 // ---- the kernel -------------------------------------------------------------
 // STOP: the build with learned-stop checks and trace recording (the plain
 // search is compiled without them and keeps its smaller register budget).
+// STOP builds copy the stop network to shared memory once per block, so they
+// run large blocks: one block of 32 warps per SM at 64 registers, or for the
+// fp32 128-d variant (which spills below about 80 registers) 3 blocks of 8
+// warps.
+template <int ST, int CPL>
+constexpr bool stop_wide_regs() { return ST == HNSW_F32 && CPL == 4; }
+
 template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP>
-__global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 8) : 0) hnsw_search_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : 1024) : 128,
+                                  STOP ? (stop_wide_regs<ST, CPL>() ? 3 : 1) : 0) hnsw_search_kernel(const SearchArgs a) {
     using D = Dist<ST, TEAM, CPL, U, FULL>;
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -575,6 +583,16 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
     uint32_t* nbuf = reinterpret_cast<uint32_t*>(qs + ix_row32(a));  // staged neighbour row (16-byte aligned)
     const DevIndex& ix = a.ix;
     const int hsz = 1 << a.hlog;
+    // the stop network, one copy per block after the warps' regions
+    const StopDev* model = nullptr;
+    if (STOP && a.stop) {
+        StopDev* m = reinterpret_cast<StopDev*>(smem + (blockDim.x >> 5) * a.warp_smem);
+        const uint4* src = reinterpret_cast<const uint4*>(a.stop);
+        uint4* d4 = reinterpret_cast<uint4*>(m);
+        for (int i = threadIdx.x; i < int(sizeof(StopDev) / 16); i += blockDim.x) d4[i] = src[i];
+        __syncthreads();
+        model = m;
+    }
     for (;;) {
         uint32_t qi = 0;
         if (lane == 0) qi = atomicAdd(a.work, 1u);
@@ -661,8 +679,9 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
             int scan = 0;
             const int deg = int(ix.Mmax0);
             const float d1 = key_dist(cur);  // where the upper-layer descent ended
-            uint64_t last_kth = ~0ull;        // (dist, id) of the K-th best entry so far
+            const float inv_d1 = 1.0f / fmaxf(d1, 1e-12f);
             uint32_t stale = 0, n_eval0 = 0;
+            int until_check = STOP ? a.stop_period : 0;  // expansions left to the next check
             uint32_t nxt_id = kNone;  // element whose neighbour row is staged in nbuf
             __syncwarp();
             for (;;) {
@@ -755,24 +774,19 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
                 scan = min(p + 1, first_new);
                 if (STOP && a.stop_period > 0) {
                     const int kq = a.q_kef ? int(__ldg(a.q_kef + qi) & 0xffffu) : a.k;
-                    // the top-K of W changes exactly when its K-th key decreases
-                    const uint64_t kthk = size >= kq ? (W[kq - 1] >> 1) : ~0ull;
-                    if (kthk < last_kth) {
-                        last_kth = kthk;
-                        stale = 0;
-                    } else {
-                        ++stale;
-                    }
-                    if (size >= kq && n_exp0 % uint32_t(a.stop_period) == 0) {
-                        const float d1n = fmaxf(d1, 1e-12f);
+                    // expansions since an element entered the K nearest of W (once W
+                    // holds K entries: since its K-th key last decreased)
+                    stale = first_new < kq ? 0u : stale + 1u;
+                    if (--until_check == 0) until_check = a.stop_period;
+                    if (size >= kq && until_check == a.stop_period) {
                         float f[kStopIn];
-                        f[0] = log1pf(fmaxf(key_dist(W[0]) / d1n, 0.0f));
-                        f[1] = log1pf(fmaxf(key_dist(W[size - 1]) / d1n, 0.0f));
+                        f[0] = log1pf(fmaxf(key_dist(W[0]) * inv_d1, 0.0f));
+                        f[1] = log1pf(fmaxf(key_dist(W[size - 1]) * inv_d1, 0.0f));
                         f[2] = log1pf(float(n_eval0));
                         f[3] = log1pf(fmaxf(d1, 0.0f));
                         f[4] = log1pf(float(stale));
-                        f[5] = log1pf(fmaxf(key_dist(W[kq - 1]) / d1n, 0.0f));
-                        const float logit = a.stop ? stop_logit(a.stop, f, reinterpret_cast<float*>(ck), lane) : 0.0f;
+                        f[5] = log1pf(fmaxf(key_dist(W[kq - 1]) * inv_d1, 0.0f));
+                        const float logit = model ? stop_logit(model, f, reinterpret_cast<float*>(ck), lane) : 0.0f;
                         if (a.tr_count) {
                             if (n_checks < a.tr_max) {
                                 const uint64_t slot = uint64_t(qi) * uint64_t(a.tr_max) + uint64_t(n_checks);
@@ -784,7 +798,7 @@ __global__ void __launch_bounds__(128, STOP ? (ST == HNSW_F32 && CPL == 4 ? 7 : 
                                 for (int i = lane; i < a.k; i += 32) a.tr_topk[slot * uint64_t(a.k) + i] = key_id(W[i]);
                             }
                             ++n_checks;
-                        } else if (a.stop && logit > a.stop_logit) {
+                        } else if (model && logit > a.stop_logit) {
                             flags |= 2u;  // learned stop: W's top-K is predicted final
                             if (nxt_id != kNone) cp_async_wait_all();
                             __syncwarp();
@@ -987,9 +1001,18 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
     const size_t per_warp = size_t(a.efcap) * 8 + (size_t(1) << a.hlog) * 4 + kMaxDeg * (4 + 4 + 8 + 4) +
                             size_t(D.row_chunks32) * 16 + kMaxDeg * 4;
     a.warp_smem = int((per_warp + 15) & ~size_t(15));
+    const bool stop_build = stop != nullptr && stop->period > 0;
+    const size_t model_smem = (stop_build && stop->stop) ? sizeof(StopDev) : 0;
     int warps = 4;
-    while (warps > 1 && size_t(warps) * a.warp_smem > 227 * 1024) warps >>= 1;
-    const size_t smem = size_t(warps) * a.warp_smem;
+    if (stop_build) {
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, kc.fn);
+        if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("search: attributes: ") + cudaGetErrorString(e));
+        warps = fa.maxThreadsPerBlock / 32;
+        while (warps > 1 && size_t(warps) * a.warp_smem + model_smem > 227 * 1024) --warps;
+    }
+    while (warps > 1 && size_t(warps) * a.warp_smem + model_smem > 227 * 1024) warps >>= 1;
+    const size_t smem = size_t(warps) * a.warp_smem + model_smem;
     if (smem > 227 * 1024) return fail(HNSW_EINVAL, "search: ef/visited set too large for shared memory");
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);

@@ -37,41 +37,27 @@ struct StopDev {
 };
 static_assert(sizeof(StopDev) % 16 == 0, "StopDev is copied in 16-byte words");
 
-// read-only load kept in L1 in preference to streaming data
-__device__ __forceinline__ float4 ld_w4(const float4* p) {
-    float4 v;
-    asm volatile("ld.global.nc.L1::evict_last.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
-    return v;
-}
-__device__ __forceinline__ unsigned ld_w1(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-}
-
 // Logit of the network for features f (identical in every lane), computed by
-// one warp: lane l owns hidden units l and l + 32.  The first hidden layer is
-// exchanged through a 64-float scratch `hs` in shared memory and read back
-// with 16-byte broadcast loads.
+// one warp from the block's shared-memory copy m of the network: lane l owns
+// hidden units l and l + 32.  The first hidden layer is exchanged through a
+// 64-float scratch `hs` in shared memory and read back with 16-byte
+// broadcast loads.
 __device__ __forceinline__ float stop_logit(const StopDev* __restrict__ m, const float (&f)[kStopIn],
                                             float* hs, int lane) {
     float xn[kStopIn];
 #pragma unroll
-    for (int i = 0; i < kStopIn; ++i) xn[i] = (f[i] - __ldg(&m->mu[i])) * __ldg(&m->isig[i]);
-    float ha = __ldg(&m->b1[lane]), hb = __ldg(&m->b1[lane + 32]);
+    for (int i = 0; i < kStopIn; ++i) xn[i] = (f[i] - m->mu[i]) * m->isig[i];
+    float ha = m->b1[lane], hb = m->b1[lane + 32];
 #pragma unroll
     for (int i = 0; i < kStopIn; ++i) {
-        ha = fmaf(__ldg(&m->w1[lane * kStopIn + i]), xn[i], ha);
-        hb = fmaf(__ldg(&m->w1[(lane + 32) * kStopIn + i]), xn[i], hb);
+        ha = fmaf(m->w1[lane * kStopIn + i], xn[i], ha);
+        hb = fmaf(m->w1[(lane + 32) * kStopIn + i], xn[i], hb);
     }
     __syncwarp();
     hs[lane] = fmaxf(ha, 0.0f);
     hs[lane + 32] = fmaxf(hb, 0.0f);
     __syncwarp();
-    float za = __ldg(&m->b2[lane]), zb = __ldg(&m->b2[lane + 32]);
-    const unsigned* w2 = reinterpret_cast<const unsigned*>(m->w2p);
+    float za = m->b2[lane], zb = m->b2[lane + 32];
     const float4* h4 = reinterpret_cast<const float4*>(hs);
 #pragma unroll 4
     for (int u4 = 0; u4 < kStopH / 4; ++u4) {
@@ -79,18 +65,15 @@ __device__ __forceinline__ float stop_logit(const StopDev* __restrict__ m, const
         const float hv[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const unsigned bits = ld_w1(w2 + (u4 * 4 + j) * 32 + lane);
-            __half2 w;
-            memcpy(&w, &bits, 4);
-            const float2 wf = __half22float2(w);
+            const float2 wf = __half22float2(m->w2p[(u4 * 4 + j) * 32 + lane]);
             za = fmaf(wf.x, hv[j], za);
             zb = fmaf(wf.y, hv[j], zb);
         }
     }
-    float o = __ldg(&m->w3[lane]) * fmaxf(za, 0.0f) + __ldg(&m->w3[lane + 32]) * fmaxf(zb, 0.0f);
+    float o = m->w3[lane] * fmaxf(za, 0.0f) + m->w3[lane + 32] * fmaxf(zb, 0.0f);
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
-    return o + __ldg(&m->b3);
+    return o + m->b3;
 }
 
 }  // namespace hnswgb
