@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "QPS at recall@10≥0.95, 1M×128, chosen vs plain GPU form; % of HBM-gather roofline"
-EF_SWEEP = [10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 400]
+EF_SWEEP = [10, 12, 16, 20, 24, 32, 36, 40, 44, 48, 52, 56, 60, 64, 72, 80, 88, 96, 112, 128, 160, 192, 256, 320, 400]
 
 
 def max_over_ranks(ms: float, pg) -> float:
@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--threads", type=int, default=0, help="builder threads (0: all)")
     ap.add_argument("--forms", default="f32,bf16r,fp8r,bf16r_stop")
     ap.add_argument("--train-queries", type=int, default=20_000, help="learned stop: training queries")
-    ap.add_argument("--stop-efs", type=lambda v: [int(x) for x in v.split(",")], default=[64, 80, 96])
+    ap.add_argument("--stop-efs", type=lambda v: [int(x) for x in v.split(",")], default=[56, 64, 80])
     ap.add_argument("--stop-thresholds", type=lambda v: [float(x) for x in v.split(",")],
                     default=[0.5, 0.7, 0.8, 0.85, 0.9, 0.95, 0.98])
     ap.add_argument("--stop-period", type=int, default=8)

@@ -170,7 +170,8 @@ typedef struct {
                                 network's sigmoid exceeds it (needs hnsw_set_stop_model);
                                 <= 0 or >= 1: off, the plain search */
     int32_t stop_period;     /* learned stop / trace: check every stop_period layer-0
-                                expansions (<= 0: 8 for the stop, 4 for traces) */
+                                expansions (<= 0: 8 for the stop, 4 for traces;
+                                above 65535: HNSW_EINVAL) */
     int32_t schedule;        /* 0: automatic -- batches larger than four times the kernel's
                                 resident warps run in two passes, the upper-layer descent of all
                                 queries first, then the layer-0 beams in order of
@@ -194,7 +195,8 @@ hnsw_status hnsw_search_ex(hnsw_index* index, const hnsw_search_params* params,
  * the current top-k of W is already final.  Features (d1 = distance of the
  * element where the upper-layer descent ended, clamped below by 1e-12):
  * log1p(best/d1), log1p(worst/d1), log1p(layer-0 distance evaluations),
- * log1p(d1), log1p(expansions since the k-th best entry last improved),
+ * log1p(d1), log1p(expansions since the k-th best entry last improved,
+ * saturating at 65535),
  * log1p(kth/d1), where best/worst/kth are distances of W's entries.
  * Weights: 4,673 fp16 values in the order W1 (64x6, row-major out x in), b1,
  * W2 (64x64), b2, w3 (64), b3; normalisation: mean[6] then std[6], applied as

@@ -69,6 +69,16 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 #ifndef HNSW_MIN_BLOCKS
 #define HNSW_MIN_BLOCKS 0
 #endif
+// HNSW_STOP_NOINLINE: the stop check (features + network) as a called
+// function instead of inline code in the layer-0 loop
+#ifndef HNSW_STOP_NOINLINE
+#define HNSW_STOP_NOINLINE 0
+#endif
+#if HNSW_STOP_NOINLINE
+#define HNSW_STOP_FN __device__ __noinline__
+#else
+#define HNSW_STOP_FN __device__ __forceinline__
+#endif
 // rows gathered per team and round for fp32 rows of 128 coordinates and for
 // bf16/f16 rows of up to 128 coordinates
 #ifndef HNSW_F32_U
@@ -559,6 +569,27 @@ __device__ __forceinline__ uint32_t ix_row32(const SearchArgs& a) { return a.ix.
 // ---- the kernel -------------------------------------------------------------
 // STOP: the build with learned-stop checks and trace recording (the plain
 // search is compiled without them and keeps its smaller register budget).
+// One learned-stop check of a warp's search: the six features of the state
+// of W (aux: 1/d1, log1p(d1), layer-0 distance evaluations at entry) written
+// to aux[4..9], and the network's logit (0 without a network).  log1p of the
+// per-check features is taken as log(1 + x) with the fast logarithm.
+HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size, int kq, float* aux,
+                              uint32_t n_eval0, uint32_t stale, float* hs, int lane) {
+    const float inv_d1 = aux[0];
+    float f[kStopIn];
+    f[0] = __logf(1.0f + fmaxf(key_dist(W[0]) * inv_d1, 0.0f));
+    f[1] = __logf(1.0f + fmaxf(key_dist(W[size - 1]) * inv_d1, 0.0f));
+    f[2] = __logf(1.0f + float(n_eval0));
+    f[3] = aux[1];
+    f[4] = __logf(1.0f + float(stale));
+    f[5] = __logf(1.0f + fmaxf(key_dist(W[kq - 1]) * inv_d1, 0.0f));
+    float fv = f[0];
+#pragma unroll
+    for (int i = 1; i < kStopIn; ++i) fv = lane == i ? f[i] : fv;
+    if (lane < kStopIn) aux[4 + lane] = fv;
+    return model ? stop_logit(model, f, hs, lane) : 0.0f;
+}
+
 // STOP builds copy the stop network to shared memory once per block, so they
 // run large blocks: one block of 32 warps per SM at 64 registers, or for the
 // fp32 128-d variant (which spills below about 80 registers) 3 blocks of 8
@@ -566,8 +597,12 @@ __device__ __forceinline__ uint32_t ix_row32(const SearchArgs& a) { return a.ix.
 template <int ST, int CPL>
 constexpr bool stop_wide_regs() { return ST == HNSW_F32 && CPL == 4; }
 
+#ifndef HNSW_STOP_THREADS
+#define HNSW_STOP_THREADS 1024
+#endif
+
 template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP>
-__global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : 1024) : 128,
+__global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW_STOP_THREADS) : 128,
                                   STOP ? (stop_wide_regs<ST, CPL>() ? 3 : 1) : 0) hnsw_search_kernel(const SearchArgs a) {
     using D = Dist<ST, TEAM, CPL, U, FULL>;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -581,17 +616,20 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : 1024
     uint32_t* lbs = reinterpret_cast<uint32_t*>(ck + kMaxDeg);
     float* qs = reinterpret_cast<float*>(lbs + kMaxDeg);
     uint32_t* nbuf = reinterpret_cast<uint32_t*>(qs + ix_row32(a));  // staged neighbour row (16-byte aligned)
+    // per-query scalars read only at stop checks (kept out of registers):
+    // 1/d1, log1p(d1), n_eval at layer 0 entry, checks recorded; [4..9] the
+    // features of the last check
+    float* aux = reinterpret_cast<float*>(nbuf + kMaxDeg);
+    uint32_t* n_checks = reinterpret_cast<uint32_t*>(aux + 3);
     const DevIndex& ix = a.ix;
     const int hsz = 1 << a.hlog;
-    // the stop network, one copy per block after the warps' regions
-    const StopDev* model = nullptr;
+    // the stop network, one copy per block after the warps' regions (its
+    // address is recomputed at each check rather than held in registers)
     if (STOP && a.stop) {
-        StopDev* m = reinterpret_cast<StopDev*>(smem + (blockDim.x >> 5) * a.warp_smem);
+        uint4* d4 = reinterpret_cast<uint4*>(smem + (blockDim.x >> 5) * a.warp_smem);
         const uint4* src = reinterpret_cast<const uint4*>(a.stop);
-        uint4* d4 = reinterpret_cast<uint4*>(m);
         for (int i = threadIdx.x; i < int(sizeof(StopDev) / 16); i += blockDim.x) d4[i] = src[i];
         __syncthreads();
-        model = m;
     }
     for (;;) {
         uint32_t qi = 0;
@@ -614,7 +652,7 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : 1024
         for (int i = lane; i < (hsz >> 2); i += 32)
             reinterpret_cast<uint4*>(H)[i] = make_uint4(kNone, kNone, kNone, kNone);
         uint32_t n_eval = 0, n_exp0 = 0, n_stepU = 0, flags = 0;
-        int n_checks = 0;
+        if (STOP && lane == 0) *n_checks = 0;
         int size = 0;
         __syncwarp();
         if (ix.N > 0) {
@@ -678,10 +716,15 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : 1024
             size = 1;
             int scan = 0;
             const int deg = int(ix.Mmax0);
-            const float d1 = key_dist(cur);  // where the upper-layer descent ended
-            const float inv_d1 = 1.0f / fmaxf(d1, 1e-12f);
-            uint32_t stale = 0, n_eval0 = 0;
-            int until_check = STOP ? a.stop_period : 0;  // expansions left to the next check
+            if (STOP && lane == 0) {
+                const float d1 = key_dist(cur);  // where the upper-layer descent ended
+                aux[0] = 1.0f / fmaxf(d1, 1e-12f);
+                aux[1] = log1pf(fmaxf(d1, 0.0f));
+                aux[2] = __uint_as_float(n_eval);
+            }
+            // stale (expansions since the K nearest of W last changed) in the
+            // high half, expansions left to the next check in the low half
+            uint32_t stale_cd = STOP ? uint32_t(a.stop_period) : 0u;
             uint32_t nxt_id = kNone;  // element whose neighbour row is staged in nbuf
             __syncwarp();
             for (;;) {
@@ -766,7 +809,6 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : 1024
                     D::run(ix, qr, ids, n, dst, lane);
                     __syncwarp();
                     n_eval += n;
-                    n_eval0 += n;
                     first_new = (a.efcap <= 64 && n <= 32)
                                     ? merge_small(W, size, efq, ids, dst, n, lane)
                                     : merge_batch(W, size, efq, ids, dst, n, ck, lbs, lane);
@@ -774,30 +816,30 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : 1024
                 scan = min(p + 1, first_new);
                 if (STOP && a.stop_period > 0) {
                     const int kq = a.q_kef ? int(__ldg(a.q_kef + qi) & 0xffffu) : a.k;
-                    // expansions since an element entered the K nearest of W (once W
-                    // holds K entries: since its K-th key last decreased)
-                    stale = first_new < kq ? 0u : stale + 1u;
-                    if (--until_check == 0) until_check = a.stop_period;
-                    if (size >= kq && until_check == a.stop_period) {
-                        float f[kStopIn];
-                        f[0] = log1pf(fmaxf(key_dist(W[0]) * inv_d1, 0.0f));
-                        f[1] = log1pf(fmaxf(key_dist(W[size - 1]) * inv_d1, 0.0f));
-                        f[2] = log1pf(float(n_eval0));
-                        f[3] = log1pf(fmaxf(d1, 0.0f));
-                        f[4] = log1pf(float(stale));
-                        f[5] = log1pf(fmaxf(key_dist(W[kq - 1]) * inv_d1, 0.0f));
-                        const float logit = model ? stop_logit(model, f, reinterpret_cast<float*>(ck), lane) : 0.0f;
+                    // stale: expansions since an element entered the K nearest of W
+                    // (once W holds K entries: since its K-th key last decreased),
+                    // saturating at 65535
+                    stale_cd = first_new < kq ? (stale_cd & 0xffffu) : __vaddus2(stale_cd, 0x10000u);
+                    stale_cd -= 1u;
+                    const bool check = (stale_cd & 0xffffu) == 0u;
+                    if (check) stale_cd |= uint32_t(a.stop_period);
+                    if (size >= kq && check) {
+                        __syncwarp();
+                        const StopDev* model =
+                            a.stop ? reinterpret_cast<const StopDev*>(smem + (blockDim.x >> 5) * a.warp_smem) : nullptr;
+                        const float logit = stop_check(model, W, size, kq, aux, n_eval - __float_as_uint(aux[2]),
+                                                       stale_cd >> 16, reinterpret_cast<float*>(ck), lane);
                         if (a.tr_count) {
-                            if (n_checks < a.tr_max) {
-                                const uint64_t slot = uint64_t(qi) * uint64_t(a.tr_max) + uint64_t(n_checks);
-                                float fv = f[0];
-#pragma unroll
-                                for (int i = 1; i < kStopIn; ++i) fv = lane == i ? f[i] : fv;
-                                if (lane < kStopIn) a.tr_feat[slot * kStopIn + lane] = fv;
+                            __syncwarp();
+                            const uint32_t c = *n_checks;
+                            if (c < uint32_t(a.tr_max)) {
+                                const uint64_t slot = uint64_t(qi) * uint64_t(a.tr_max) + c;
+                                if (lane < kStopIn) a.tr_feat[slot * kStopIn + lane] = aux[4 + lane];
                                 if (lane == 0 && a.tr_logit) a.tr_logit[slot] = logit;
                                 for (int i = lane; i < a.k; i += 32) a.tr_topk[slot * uint64_t(a.k) + i] = key_id(W[i]);
                             }
-                            ++n_checks;
+                            __syncwarp();
+                            if (lane == 0) *n_checks = c + 1;
                         } else if (model && logit > a.stop_logit) {
                             flags |= 2u;  // learned stop: W's top-K is predicted final
                             if (nxt_id != kNone) cp_async_wait_all();
@@ -836,7 +878,7 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : 1024
             a.out_ids[obase + i] = oid;
             a.out_dists[obase + i] = od;
         }
-        if (STOP && a.tr_count && lane == 0) a.tr_count[qi] = n_checks < a.tr_max ? n_checks : a.tr_max;
+        if (STOP && a.tr_count && lane == 0) a.tr_count[qi] = int(min(*n_checks, uint32_t(a.tr_max)));
         if (a.stats && lane == 0) {
             hnsw_query_stats s;
             s.n_eval = n_eval;
@@ -999,7 +1041,7 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
         a.tr_max = stop->tr_max;
     }
     const size_t per_warp = size_t(a.efcap) * 8 + (size_t(1) << a.hlog) * 4 + kMaxDeg * (4 + 4 + 8 + 4) +
-                            size_t(D.row_chunks32) * 16 + kMaxDeg * 4;
+                            size_t(D.row_chunks32) * 16 + kMaxDeg * 4 + 64;
     a.warp_smem = int((per_warp + 15) & ~size_t(15));
     const bool stop_build = stop != nullptr && stop->period > 0;
     const size_t model_smem = (stop_build && stop->stop) ? sizeof(StopDev) : 0;
@@ -1081,6 +1123,7 @@ hnsw_status search_group(hnsw_index* ix, const hnsw_search_params& p, const floa
     if (max_k < 1 || max_k > kMaxK || (max_ef > max_k ? max_ef : max_k) > kMaxEf)
         return fail(HNSW_EINVAL, "search group: k or ef out of range");
     if (p.rerank && !ix->dev.vec32) return fail(HNSW_EINVAL, "search group: rerank needs the fp32 copy");
+    if (p.stop_period > 65535) return fail(HNSW_EINVAL, "search group: stop_period above 65535");
     StopModel sm{};
     const StopModel* smp = nullptr;
     if (p.stop_threshold > 0.0f && p.stop_threshold < 1.0f) {
@@ -1107,6 +1150,7 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     if (p->visited_log2 != 0 && (p->visited_log2 < 5 || p->visited_log2 > 15))
         return fail(HNSW_EINVAL, "hnsw_search: visited_log2 outside [5,15]");
     if (p->rerank && !ix->dev.vec32) return fail(HNSW_EINVAL, "hnsw_search: rerank needs the fp32 copy");
+    if (p->stop_period > 65535) return fail(HNSW_EINVAL, "hnsw_search: stop_period above 65535");
     if (n == 0) return HNSW_OK;
     if (!queries || !out_ids || !out_dists) return fail(HNSW_EINVAL, "hnsw_search: null buffer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1230,6 +1274,7 @@ extern "C" hnsw_status hnsw_search_trace(hnsw_index* ix, const hnsw_search_param
         if (!is_device_ptr(q)) return fail(HNSW_EINVAL, "hnsw_search_trace: buffers must be device memory");
     if ((logits && !is_device_ptr(logits)) || (stats && !is_device_ptr(stats)))
         return fail(HNSW_EINVAL, "hnsw_search_trace: buffers must be device memory");
+    if (p->stop_period > 65535) return fail(HNSW_EINVAL, "hnsw_search_trace: stop_period above 65535");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     StopModel sm{};
     sm.stop = logits ? ix->d_stop : nullptr;

@@ -388,14 +388,19 @@ extern "C" hnsw_status hnsw_set_stop_model(hnsw_index* ix, const float* norm, co
         r.x = w_fp16[i];
         return __half(r);
     };
-    for (int i = 0; i < kStopIn; ++i) {
+    for (int i = 0; i < kStopIn; ++i)
         if (!(norm[kStopIn + i] > 0)) return fail(HNSW_EINVAL, "hnsw_set_stop_model: sigma must be > 0");
-        h.mu[i] = norm[i];
-        h.isig[i] = 1.0f / norm[kStopIn + i];
+    // (x - mu) / sigma folded into the first layer
+    for (int j = 0; j < kStopH; ++j) {
+        double b = double(__half2float(f16(kOffB1 + j)));
+        for (int i = 0; i < kStopIn; ++i) {
+            const double w = double(__half2float(f16(kOffW1 + j * kStopIn + i))) / double(norm[kStopIn + i]);
+            h.w1[j * kStopIn + i] = float(w);
+            b -= w * double(norm[i]);
+        }
+        h.b1[j] = float(b);
     }
-    for (int i = 0; i < kStopH * kStopIn; ++i) h.w1[i] = __half2float(f16(kOffW1 + i));
     for (int i = 0; i < kStopH; ++i) {
-        h.b1[i] = __half2float(f16(kOffB1 + i));
         h.b2[i] = __half2float(f16(kOffB2 + i));
         h.w3[i] = __half2float(f16(kOffW3 + i));
     }

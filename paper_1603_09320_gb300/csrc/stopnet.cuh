@@ -21,12 +21,12 @@ constexpr int kStopH = 64;
 constexpr int kStopParams = kStopIn * kStopH + kStopH + kStopH * kStopH + kStopH + kStopH + 1;  // 4673
 constexpr int kOffW1 = 0, kOffB1 = 384, kOffW2 = 448, kOffB2 = 4544, kOffW3 = 4608, kOffB3 = 4672;
 
-// Inference layout on the device: the small tensors widened to fp32 (exact),
-// W2 kept in fp16 as pairs (W2[l][u], W2[l+32][u]) so that lane l of a warp
-// reads one 4-byte word per input u.
+// Inference layout on the device: the input normalisation folded into the
+// first layer (w1[j][i] = W1[j][i] / sigma[i], b1[j] - sum_i w1[j][i] mu[i],
+// computed in double and rounded to fp32), the other small tensors widened to
+// fp32 (exact), W2 kept in fp16 as pairs (W2[l][u], W2[l+32][u]) so that lane
+// l of a warp reads one 4-byte word per input u.
 struct StopDev {
-    float mu[kStopIn];
-    float isig[kStopIn];
     float w1[kStopH * kStopIn];
     float b1[kStopH];
     float b2[kStopH];
@@ -44,32 +44,37 @@ static_assert(sizeof(StopDev) % 16 == 0, "StopDev is copied in 16-byte words");
 // broadcast loads.
 __device__ __forceinline__ float stop_logit(const StopDev* __restrict__ m, const float (&f)[kStopIn],
                                             float* hs, int lane) {
-    float xn[kStopIn];
-#pragma unroll
-    for (int i = 0; i < kStopIn; ++i) xn[i] = (f[i] - m->mu[i]) * m->isig[i];
     float ha = m->b1[lane], hb = m->b1[lane + 32];
 #pragma unroll
     for (int i = 0; i < kStopIn; ++i) {
-        ha = fmaf(m->w1[lane * kStopIn + i], xn[i], ha);
-        hb = fmaf(m->w1[(lane + 32) * kStopIn + i], xn[i], hb);
+        ha = fmaf(m->w1[lane * kStopIn + i], f[i], ha);
+        hb = fmaf(m->w1[(lane + 32) * kStopIn + i], f[i], hb);
     }
     __syncwarp();
     hs[lane] = fmaxf(ha, 0.0f);
     hs[lane + 32] = fmaxf(hb, 0.0f);
     __syncwarp();
-    float za = m->b2[lane], zb = m->b2[lane + 32];
+    // two accumulators per output (even and odd inputs) halve the FMA chains
+    float za = m->b2[lane], zb = m->b2[lane + 32], za1 = 0.0f, zb1 = 0.0f;
     const float4* h4 = reinterpret_cast<const float4*>(hs);
 #pragma unroll 4
     for (int u4 = 0; u4 < kStopH / 4; ++u4) {
         const float4 h = h4[u4];
-        const float hv[4] = {h.x, h.y, h.z, h.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float2 wf = __half22float2(m->w2p[(u4 * 4 + j) * 32 + lane]);
-            za = fmaf(wf.x, hv[j], za);
-            zb = fmaf(wf.y, hv[j], zb);
-        }
+        const float2 w0 = __half22float2(m->w2p[(u4 * 4 + 0) * 32 + lane]);
+        const float2 w1 = __half22float2(m->w2p[(u4 * 4 + 1) * 32 + lane]);
+        const float2 w2 = __half22float2(m->w2p[(u4 * 4 + 2) * 32 + lane]);
+        const float2 w3 = __half22float2(m->w2p[(u4 * 4 + 3) * 32 + lane]);
+        za = fmaf(w0.x, h.x, za);
+        zb = fmaf(w0.y, h.x, zb);
+        za1 = fmaf(w1.x, h.y, za1);
+        zb1 = fmaf(w1.y, h.y, zb1);
+        za = fmaf(w2.x, h.z, za);
+        zb = fmaf(w2.y, h.z, zb);
+        za1 = fmaf(w3.x, h.w, za1);
+        zb1 = fmaf(w3.y, h.w, zb1);
     }
+    za += za1;
+    zb += zb1;
     float o = m->w3[lane] * fmaxf(za, 0.0f) + m->w3[lane + 32] * fmaxf(zb, 0.0f);
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
