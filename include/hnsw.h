@@ -143,8 +143,11 @@ hnsw_status hnsw_get_index_info(const hnsw_index* index, hnsw_index_info* out);
  * slots beyond the reachable elements hold HNSW_NO_ID / +inf.
  * Pointers may be host or device memory (detected per pointer).  With only
  * device pointers the call is asynchronous on `stream`; if any pointer is
- * host memory the call copies through library-owned device buffers and
- * synchronises `stream` before returning.
+ * host memory the call copies through a library-owned device buffer of that
+ * stream (one per stream, for up to 16 streams per index) and synchronises
+ * `stream` before returning.  Calls on different streams may run
+ * concurrently from several host threads; concurrent host-memory calls on
+ * one index and one stream are not supported.
  * Errors: HNSW_EINVAL (null index/pointers with n > 0, k < 1, ef < 1, n < 0,
  * k > 1024, ef' > the kernel limit 1024), HNSW_ECUDA. */
 hnsw_status hnsw_search(hnsw_index* index, const float* queries, int64_t n, int32_t k, int32_t ef,

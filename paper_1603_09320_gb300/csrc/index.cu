@@ -212,9 +212,11 @@ extern "C" hnsw_status hnsw_upload_index(const void* graph_blob, uint64_t blob_b
 
 extern "C" hnsw_status hnsw_free_index(hnsw_index* ix) {
     if (!ix) return HNSW_OK;
-    void* ptrs[] = {ix->d_vec, ix->d_scale, ix->d_nbr0, ix->d_upoff, ix->d_nbrU, ix->d_work, ix->d_stop, ix->stage};
+    void* ptrs[] = {ix->d_vec, ix->d_scale, ix->d_nbr0, ix->d_upoff, ix->d_nbrU, ix->d_work, ix->d_stop};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (auto& st : ix->stages)
+        if (st.buf) cudaFree(st.buf);
     if (ix->d_vec32 && ix->d_vec32 != ix->d_vec) cudaFree(ix->d_vec32);
     delete ix;
     return HNSW_OK;

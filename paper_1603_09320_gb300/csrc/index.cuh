@@ -18,12 +18,15 @@
 
 #include <atomic>
 #include <cstdint>
+#include <mutex>
+#include <vector>
 
 #include "../../include/hnsw.h"
 
 namespace hnswgb {
 
 constexpr int kWorkSlots = 1024;
+constexpr int kMaxStages = 16;  // streams with their own host-memory staging buffer
 constexpr int kMaxEf = 1024;   // ef' limit of the search kernel
 constexpr int kMaxK = 1024;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
@@ -72,8 +75,16 @@ struct hnsw_index {
     uint32_t* d_work = nullptr;
     void* d_stop = nullptr;  // learned-stop weights (fp16), or null
     std::atomic<uint32_t> work_next{0};
-    // staging for host-memory queries/results, grown on demand
-    void* stage = nullptr;
-    size_t stage_bytes = 0;
+    // staging for host-memory queries/results: one device buffer per stream
+    // (grown on demand, at most kMaxStages streams; the oldest idle one is
+    // dropped to make room)
+    struct Stage {
+        void* stream;
+        void* buf;
+        size_t bytes;
+        int in_use;  // calls between taking the buffer and their final synchronisation
+    };
+    std::mutex stage_mu;
+    std::vector<Stage> stages;
     int device = 0;
 };

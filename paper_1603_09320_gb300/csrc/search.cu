@@ -1154,6 +1154,17 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     if (n == 0) return HNSW_OK;
     if (!queries || !out_ids || !out_dists) return fail(HNSW_EINVAL, "hnsw_search: null buffer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // releases this call's hold on its stream's staging buffer on every return
+    struct StageLease {
+        hnsw_index* ix = nullptr;
+        void* stream = nullptr;
+        ~StageLease() {
+            if (!ix) return;
+            std::lock_guard<std::mutex> lk(ix->stage_mu);
+            for (auto& st : ix->stages)
+                if (st.stream == stream && st.in_use > 0) --st.in_use;
+        }
+    } lease;
     const bool dq = is_device_ptr(queries), di = is_device_ptr(out_ids), dd = is_device_ptr(out_dists);
     const bool ds = stats ? is_device_ptr(stats) : true;
     const size_t qb = size_t(n) * ix->dev.d * 4, ob = size_t(n) * p->k * 4, sb = stats ? size_t(n) * 16 : 0;
@@ -1163,20 +1174,44 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     hnsw_query_stats* st = stats;
     if (!dq || !di || !dd || !ds) {
         const size_t need = al256(qb) + 2 * al256(ob) + al256(sb);
-        if (ix->stage_bytes < need) {
-            if (ix->stage) {
-                cudaStreamSynchronize(s);
-                cudaFree(ix->stage);
-                ix->stage = nullptr;
-                ix->stage_bytes = 0;
+        void* sbuf = nullptr;
+        {
+            // this stream's staging buffer (calls on different streams may run
+            // concurrently; cudaFree synchronises the device before a buffer
+            // is replaced or dropped, and only idle buffers are dropped)
+            std::lock_guard<std::mutex> lk(ix->stage_mu);
+            hnsw_index::Stage* e = nullptr;
+            for (auto& st : ix->stages)
+                if (st.stream == stream) e = &st;
+            if (!e) {
+                if (int(ix->stages.size()) >= kMaxStages) {
+                    auto it = ix->stages.begin();
+                    while (it != ix->stages.end() && it->in_use > 0) ++it;
+                    if (it == ix->stages.end())
+                        return fail(HNSW_EINVAL, "hnsw_search: more than 16 concurrent host-memory calls on one index");
+                    if (it->buf) cudaFree(it->buf);
+                    ix->stages.erase(it);
+                }
+                ix->stages.push_back({stream, nullptr, 0, 0});
+                e = &ix->stages.back();
             }
-            if (cudaMalloc(&ix->stage, need) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(HNSW_ENOMEM, "hnsw_search: staging buffer");
+            if (e->bytes < need) {
+                if (e->buf) cudaFree(e->buf);
+                e->buf = nullptr;
+                e->bytes = 0;
+                if (cudaMalloc(&e->buf, need) != cudaSuccess) {
+                    cudaGetLastError();
+                    e->buf = nullptr;
+                    return fail(HNSW_ENOMEM, "hnsw_search: staging buffer");
+                }
+                e->bytes = need;
             }
-            ix->stage_bytes = need;
+            ++e->in_use;
+            sbuf = e->buf;
         }
-        uint8_t* sp = static_cast<uint8_t*>(ix->stage);
+        lease.ix = ix;
+        lease.stream = stream;
+        uint8_t* sp = static_cast<uint8_t*>(sbuf);
         if (!dq) {
             q = reinterpret_cast<const float*>(sp);
             cudaError_t e = cudaMemcpyAsync(sp, queries, qb, cudaMemcpyHostToDevice, s);

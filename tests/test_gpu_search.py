@@ -69,6 +69,41 @@ def test_tiny_host_pointers_and_ragged(H):
         np.testing.assert_array_equal(gi, oi[:n])
 
 
+def test_concurrent_host_memory_calls_on_streams(H):
+    # host-memory calls from several threads, each on its own stream, each
+    # with its own staging buffer: every call returns the oracle's result
+    import threading
+    import torch
+    g, X, blob = oracle_graph("tiny", 10_000)
+    Q = synth.queries("tiny", 300)
+    oi, od, _ = oracle_batch(g, Q, 10, 32)
+    ix = H.Index(blob, "f32")
+    dev = torch.cuda.current_device()
+    errors = []
+
+    def worker(t):
+        try:
+            torch.cuda.set_device(dev)
+            s = torch.cuda.Stream()
+            lo, hi = 100 * t, 100 * (t + 1)
+            for _ in range(20):
+                ids = np.empty((hi - lo, 10), dtype=np.uint32)
+                ds = np.empty((hi - lo, 10), dtype=np.float32)
+                ix.search_into(np.ascontiguousarray(Q[lo:hi]), 10, 32, ids, ds, stream=s)
+                np.testing.assert_array_equal(ids, oi[lo:hi])
+                np.testing.assert_array_equal(ds.astype(np.float64), od[lo:hi])
+        except Exception as e:  # reported on the main thread
+            errors.append(e)
+
+    ths = [threading.Thread(target=worker, args=(t,)) for t in range(3)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    ix.close()
+    assert not errors, errors[0]
+
+
 @pytest.mark.parametrize("vlog", [5, 6, 8])
 def test_lossy_visited_set_same_result(H, vlog):
     # a tiny visited set forgets elements; results must not change
