@@ -291,22 +291,30 @@ void insert(Graph& g, Ctx& cx, uint32_t q) {
     for (int lc = L; lc > l; --lc) cur = greedy(g, cx, qv, cur, lc);  // lines 5-7
     std::vector<Item> eps{cur};
     std::vector<Item> W;
-    for (int lc = std::min(L, l); lc >= 0; --lc) {  // lines 8-17
+    const int top_lc = std::min(L, l);
+    std::vector<std::vector<Item>> sels(size_t(std::max(top_lc, -1) + 1));
+    for (int lc = top_lc; lc >= 0; --lc) {  // lines 8-17
         search_layer(g, cx, qv, eps, g.p.ef_construction, lc);
         W = cx.W;
         cx.cand.assign(W.begin(), W.end());
-        std::vector<Item> sel;
+        std::vector<Item>& sel = sels[size_t(lc)];
         select_neighbors(g, cx, qv, q, cx.cand, g.p.M, lc, sel);
-        g.locks[q].lock();  // neighbourhood(q) first, then the reverse links
+        g.locks[q].lock();
         uint32_t* ql = g.list(q, lc);
         ql[0] = 0;
         for (const Item& s : sel)
             if (s.id != q) ql[1 + ql[0]++] = s.id;
         g.locks[q].unlock();
-        for (const Item& s : sel)
-            if (s.id != q) link_back(g, cx, s.id, q, lc);
         eps.swap(W);  // line 17
     }
+    // the reverse links (lines 11-16) once neighbourhood(q) is written on
+    // every layer: q is unreachable until the first of them, so no concurrent
+    // insertion can enter layer 0 at q while q's layer-0 list is still empty.
+    // Sequentially this is the same graph: a search on layer lc - 1 reads no
+    // list that the reverse links on layer lc change.
+    for (int lc = top_lc; lc >= 0; --lc)
+        for (const Item& s : sels[size_t(lc)])
+            if (s.id != q) link_back(g, cx, s.id, q, lc);
     if (l > L) {  // lines 18-19
         g.ep = q;
         g.maxlevel = l;
@@ -366,6 +374,16 @@ extern "C" hnsw_status hnsw_build(const float* data, uint64_t N, uint32_t d, hns
         if (nt == 1 || N < 2) {
             work();
         } else {
+            // the first elements one at a time: while the graph is tiny,
+            // concurrent insertions would start from an enter point whose
+            // links are not written yet and keep only the one or two elements
+            // they find
+            const uint64_t n_seq = std::min<uint64_t>(N, 1024);
+            {
+                Ctx cx(N);
+                for (uint64_t i = 1; i < n_seq; ++i) insert(g, cx, uint32_t(i));
+            }
+            next = n_seq;
             std::vector<std::thread> th;
             for (int t = 0; t < nt; ++t) th.emplace_back(work);
             for (auto& t : th) t.join();
