@@ -88,6 +88,31 @@ hnsw_status hnsw_build(const float* data, uint64_t N, uint32_t d, hnsw_metric me
                        void** out_blob, uint64_t* out_bytes);
 void hnsw_free_blob(void* blob);
 
+/* Bulk construction with the layer-0 insertions on the GPU (Alg. 1 with Alg.
+ * 4 or Alg. 3 as SELECT-NEIGHBORS; parallel construction, Section 4.1).  On
+ * layers >= 1 Alg. 1 involves only the elements of level >= 1, so a seed --
+ * every element of level >= 1 and the first min(N, 4096) elements, in id
+ * order -- is built by hnsw_build (same parameters, n_threads as given; with
+ * n_threads = 1 its upper layers are exactly Alg. 1 applied to the seed).
+ * The other elements (all of level 0) are then inserted into layer 0 on the
+ * current device in id order, in batches of at most 1/16 of the elements
+ * already inserted (64..32768): each element of a batch searches the graph as
+ * it stood before the batch (SEARCH-LAYER with ef = efConstruction on layer
+ * 0 after the upper-layer descent), links to the M neighbours its selection
+ * keeps, and each element it links to takes it into its list, shrinking the
+ * list with the same selection when it exceeds Mmax0 (over the 256 closest
+ * candidates when there are more).  Elements of one batch do not search one
+ * another, so the graph differs from sequential insertion; it has the same
+ * structure and format as hnsw_build's (validated the same way on upload).
+ * data and level_u are host memory as for hnsw_build; device memory of about
+ * the index size (fp32) plus per-batch buffers is allocated and freed inside
+ * the call; work is issued on `stream`, which is synchronised before return.
+ * Errors: those of hnsw_build; HNSW_EINVAL also for d > 256,
+ * ef_construction > 1024 or extend_candidates set; HNSW_ENOMEM, HNSW_ECUDA. */
+hnsw_status hnsw_build_gpu(const float* data, uint64_t N, uint32_t d, hnsw_metric metric,
+                           const hnsw_build_params* params, const double* level_u, void* stream,
+                           void** out_blob, uint64_t* out_bytes);
+
 /* Graph blob format "HNSWGB01" (little-endian), the interface shared with
  * other producers of graphs (e.g. test tools):
  *   header, 128 bytes:

@@ -24,7 +24,8 @@ CU_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-rel
             "-I", INCLUDE]
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", "/usr/local/cuda/include"]
 
-SOURCES = ["search.cu", "search_noalloc.cu", "index.cu", "stopnet.cu", "builder.cpp", "blob.cpp", "server.cpp"]
+SOURCES = ["search.cu", "search_noalloc.cu", "index.cu", "stopnet.cu", "gpu_build.cu", "builder.cpp", "blob.cpp",
+           "server.cpp"]
 HEADERS = ["common.hpp", "index.cuh", "stopnet.cuh"]
 
 

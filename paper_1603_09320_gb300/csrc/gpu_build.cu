@@ -1,0 +1,558 @@
+// gpu_build.cu -- bulk construction of the graph with the insertions of
+// layer-0 elements done on the GPU in batches (Alg. 1 with Alg. 4 as
+// SELECT-NEIGHBORS; parallel construction, Section 4.1).
+//
+// Decomposition.  On layers >= 1, Alg. 1 only involves elements whose level
+// is >= 1: a search on layer lc >= 1 visits only elements present there, and
+// only they receive links there.  So the graph is built in two parts:
+//  1. a seed set -- every element of level >= 1 plus the first elements of
+//     the data -- inserted in id order on the host (hnsw_build), which gives
+//     the upper layers and the seed's layer-0 links;
+//  2. the remaining elements (all of level 0) inserted into layer 0 on the
+//     GPU in batches, in id order: for a batch, every element searches the
+//     graph as it stands before the batch (Alg. 5's descent through the upper
+//     layers, then SEARCH-LAYER with ef = efConstruction on layer 0, run by the
+//     library's search kernel), selects its M links (Alg. 4 lines 9-17), and
+//     the reverse links are added per target element, which shrinks its list
+//     with Alg. 4 when it exceeds Mmax0 (Alg. 1 lines 11-16).
+// Elements of one batch do not see one another (they are linked only through
+// the elements they link to); a batch is at most 1/16 of the elements already
+// inserted, so each element searches a graph that already holds at least 94%
+// of what precedes it.  The insertion order is a permutation of Alg. 1's (seed
+// first) with batch-parallel semantics, so the graph is not the sequential
+// one: like the multi-threaded host builder it is checked by invariants and
+// recall, not element by element.
+#include <cub/cub.cuh>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.hpp"
+#include "index.cuh"
+
+namespace hnswgb {
+// defined in search.cu
+hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n,
+                          uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
+                          uint32_t* work, const StopModel* stop);
+}  // namespace hnswgb
+
+namespace {
+
+using namespace hnswgb;
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxDW = 8;      // coordinates per lane: d <= 256
+constexpr int kKeep = 256;     // closest candidates kept for a shrink
+constexpr int kKeyBuf = 512;   // candidate keys sorted at once in a shrink
+constexpr int kWarps = 4;      // most warps per block of the selection kernels
+
+__device__ __forceinline__ uint32_t f2ord(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// Per-warp shared-memory layout of the selection kernels.
+struct WarpSmem {
+    float* Rv;       // [cap][dp] vectors of the accepted elements
+    uint32_t* Rid;   // [cap]
+    float* Rd;       // [cap] their distances to the base element
+    uint8_t* flag;   // [ncap] 1 = discarded (for keepPrunedConnections)
+    uint64_t* keys;  // [kKeyBuf] shrink candidates, (ordered distance, id)
+    uint32_t* cid;   // [kKeep] sorted shrink candidates
+    float* cd;       // [kKeep]
+};
+
+__host__ __device__ inline size_t warp_smem_bytes(int cap, uint32_t dp, int ncap) {
+    size_t b = size_t(cap) * dp * 4 + size_t(cap) * 8;
+    b += (size_t(ncap) + 15) & ~size_t(15);
+    b += size_t(kKeyBuf) * 8 + size_t(kKeep) * 8;
+    return (b + 15) & ~size_t(15);
+}
+
+__device__ inline WarpSmem carve(uint8_t* base, int cap, uint32_t dp, int ncap) {
+    WarpSmem w;
+    uint8_t* p = base;
+    w.keys = reinterpret_cast<uint64_t*>(p);
+    p += size_t(kKeyBuf) * 8;
+    w.Rv = reinterpret_cast<float*>(p);
+    p += size_t(cap) * dp * 4;
+    w.Rid = reinterpret_cast<uint32_t*>(p);
+    p += size_t(cap) * 4;
+    w.Rd = reinterpret_cast<float*>(p);
+    p += size_t(cap) * 4;
+    w.cid = reinterpret_cast<uint32_t*>(p);
+    p += size_t(kKeep) * 4;
+    w.cd = reinterpret_cast<float*>(p);
+    p += size_t(kKeep) * 4;
+    w.flag = p;
+    return w;
+}
+
+// The warp's copy of row `id`: lane l holds coordinates l, l + 32, ...
+__device__ __forceinline__ void load_vec(const float* rows, uint32_t stride, uint32_t d, uint32_t id,
+                                         float (&x)[kMaxDW], int lane) {
+    const float* r = rows + uint64_t(id) * stride;
+#pragma unroll
+    for (int k = 0; k < kMaxDW; ++k) {
+        const uint32_t c = uint32_t(lane + 32 * k);
+        x[k] = c < d ? __ldg(r + c) : 0.0f;
+    }
+}
+
+// Distance between the warp's vector x and v (shared memory, dp floats);
+// every lane returns the same value.
+__device__ __forceinline__ float dist_sm(const float (&x)[kMaxDW], const float* v, uint32_t d, int metric,
+                                         int lane) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMaxDW; ++k) {
+        const uint32_t c = uint32_t(lane + 32 * k);
+        if (c < d) {
+            if (metric == HNSW_L2SQ) {
+                const float t = x[k] - v[c];
+                s = fmaf(t, t, s);
+            } else {
+                s = fmaf(x[k], v[c], s);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    return metric == HNSW_L2SQ ? s : 1.0f - s;
+}
+
+// SELECT-NEIGHBORS over candidates (cid[i], cd[i]), i < nc, sorted by
+// (distance to the base, id), into R (w.Rid/Rd/Rv), at most cap entries.
+// heuristic: Alg. 4 lines 9-14 without extendCandidates (a candidate is
+// accepted when it is closer to the base than to every element accepted
+// before it, strictly), then lines 15-17 with keep_pruned; otherwise Alg. 3
+// (the cap nearest).  Returns |R|.
+__device__ int select_links(const float* rows, uint32_t stride, uint32_t d, uint32_t dp, int metric,
+                            const uint32_t* cid, const float* cd, int nc, int cap, bool heuristic,
+                            bool keep_pruned, const WarpSmem& w, int lane) {
+    int nr = 0;
+    for (int i = 0; i < nc && nr < cap; ++i) {
+        const uint32_t e = cid[i];
+        const float de = cd[i];
+        bool good = true;
+        float x[kMaxDW];
+        if (heuristic) {
+            load_vec(rows, stride, d, e, x, lane);
+            for (int j = 0; j < nr; ++j)
+                if (!(de < dist_sm(x, w.Rv + size_t(j) * dp, d, metric, lane))) {
+                    good = false;
+                    break;
+                }
+        }
+        if (lane == 0) w.flag[i] = good ? 0 : 1;
+        if (good) {
+            if (heuristic) {
+#pragma unroll
+                for (int k = 0; k < kMaxDW; ++k) {
+                    const uint32_t c = uint32_t(lane + 32 * k);
+                    if (c < dp) w.Rv[size_t(nr) * dp + c] = x[k];
+                }
+            }
+            if (lane == 0) {
+                w.Rid[nr] = e;
+                w.Rd[nr] = de;
+            }
+            ++nr;
+        }
+        __syncwarp();
+    }
+    if (heuristic && keep_pruned)
+        for (int i = 0; i < nc && nr < cap; ++i) {
+            if (w.flag[i]) {
+                if (lane == 0) {
+                    w.Rid[nr] = cid[i];
+                    w.Rd[nr] = cd[i];
+                }
+                ++nr;
+            }
+        }
+    __syncwarp();
+    return nr;
+}
+
+__global__ void gather_rows(const float* __restrict__ rows, uint32_t stride, uint32_t d,
+                            const uint32_t* __restrict__ ids, uint32_t n, float* __restrict__ out) {
+    const uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= uint64_t(n) * d) return;
+    const uint32_t j = uint32_t(t / d), c = uint32_t(t % d);
+    out[t] = rows[uint64_t(ids[j]) * stride + c];
+}
+
+// One warp per new element b: its M links from its search result (sorted
+// (dist, id), kNone-padded), written to its layer-0 row, and one reverse
+// pair per link: key = the linked element, value = the new element and their
+// distance (pairs of unused slots get key kNone).
+__global__ void __launch_bounds__(kWarps * 32) select_forward(
+    const float* __restrict__ rows, uint32_t stride, uint32_t d, uint32_t dp, int metric,
+    const uint32_t* __restrict__ bids, uint32_t B, const uint32_t* __restrict__ res_id,
+    const float* __restrict__ res_d, int efc, int M, int heuristic, int keep_pruned, uint32_t* __restrict__ nbr0,
+    uint32_t s0, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval, float* __restrict__ pdist) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t b = blockIdx.x * nw + wib;
+    if (b >= B) return;
+    const WarpSmem w = carve(smem + wib * warp_smem_bytes(M, dp, efc), M, dp, efc);
+    const uint32_t q = bids[b];
+    const uint32_t* cid = res_id + uint64_t(b) * efc;
+    const float* cd = res_d + uint64_t(b) * efc;
+    int nc = 0;
+    for (int i = lane; i < efc; i += 32) nc += cid[i] != kNone && cid[i] != q;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nc += __shfl_xor_sync(kFull, nc, o);
+    // results are sorted with the kNone padding last; q itself is never reachable
+    const int nr = select_links(rows, stride, d, dp, metric, cid, cd, nc, M, heuristic != 0, keep_pruned != 0, w,
+                                lane);
+    for (int j = lane; j < M; j += 32) {
+        const uint64_t o = uint64_t(b) * M + j;
+        if (j < nr) {
+            nbr0[uint64_t(q) * s0 + j] = w.Rid[j];
+            pkey[o] = w.Rid[j];
+            pval[o] = q;
+            pdist[o] = w.Rd[j];
+        } else {
+            pkey[o] = kNone;
+            pval[o] = kNone;
+            pdist[o] = 0.0f;
+        }
+    }
+}
+
+__global__ void mark_segments(const uint32_t* __restrict__ skey, uint32_t n, uint32_t* __restrict__ seg,
+                              uint32_t* __restrict__ nseg) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = skey[i];
+    if (k != kNone && (i == 0 || skey[i - 1] != k)) seg[atomicAdd(nseg, 1u)] = i;
+}
+
+// warp bitonic sort of n keys (power of two) in shared memory, ascending
+__device__ void sort_keys(uint64_t* a, int n, int lane) {
+    for (int kk = 2; kk <= n; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < n; i += 32) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const uint64_t x = a[i], y = a[p];
+                    if ((x > y) == ((i & kk) == 0)) {
+                        a[i] = y;
+                        a[p] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+}
+
+// One warp per target element e (a segment of the sorted pairs): the new
+// elements linking to e join neighbourhood(e); when the list then exceeds
+// Mmax0 it is shrunk with SELECT-NEIGHBORS over the old and new members (the
+// kKeep closest to e when there are more).
+__global__ void __launch_bounds__(kWarps * 32) link_reverse(
+    const float* __restrict__ rows, uint32_t stride, uint32_t d, uint32_t dp, int metric,
+    const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx, uint32_t npairs,
+    const uint32_t* __restrict__ seg, const uint32_t* __restrict__ nseg, const uint32_t* __restrict__ pval,
+    const float* __restrict__ pdist, uint32_t* __restrict__ nbr0, uint32_t s0, int Mmax0, int heuristic,
+    int keep_pruned) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const WarpSmem w = carve(smem + wib * warp_smem_bytes(Mmax0, dp, kKeep), Mmax0, dp, kKeep);
+    const uint32_t nsegs = *nseg;
+    for (uint32_t s = blockIdx.x * nw + wib; s < nsegs; s += gridDim.x * nw) {
+        const uint32_t i0 = seg[s];
+        const uint32_t e = skey[i0];
+        uint32_t i1 = i0 + 1;
+        while (i1 < npairs && skey[i1] == e) ++i1;  // segments are short
+        uint32_t* row = nbr0 + uint64_t(e) * s0;
+        int n0 = 0;
+        for (int j = lane; j < Mmax0; j += 32) n0 += row[j] != kNone;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(kFull, n0, o);
+        const int nin = int(i1 - i0);
+        if (n0 + nin <= Mmax0) {  // room: append in insertion order
+            for (int t = lane; t < nin; t += 32) row[n0 + t] = pval[sidx[i0 + t]];
+            __syncwarp();
+            continue;
+        }
+        // candidates: the current members (distance to e recomputed) and the
+        // new ones, keeping the kKeep closest by (distance, id)
+        float x[kMaxDW];
+        load_vec(rows, stride, d, e, x, lane);
+        int nk = 0;
+        for (int j = 0; j < n0; ++j) {
+            const uint32_t c = row[j];
+            float y[kMaxDW];
+            load_vec(rows, stride, d, c, y, lane);
+            float sacc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kMaxDW; ++k) {
+                if (uint32_t(lane + 32 * k) < d) {
+                    if (metric == HNSW_L2SQ) {
+                        const float t = x[k] - y[k];
+                        sacc = fmaf(t, t, sacc);
+                    } else {
+                        sacc = fmaf(x[k], y[k], sacc);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(kFull, sacc, o);
+            const float dc = metric == HNSW_L2SQ ? sacc : 1.0f - sacc;
+            if (lane == 0) w.keys[nk] = (uint64_t(f2ord(dc)) << 32) | c;
+            ++nk;
+        }
+        uint32_t t = 0;
+        for (;;) {
+            // fill the key buffer from the incoming pairs
+            const int room = kKeyBuf - nk;
+            const int take = min(room, int(uint32_t(nin) - t));
+            for (int u = lane; u < take; u += 32) {
+                const uint32_t pi = sidx[i0 + t + u];
+                w.keys[nk + u] = (uint64_t(f2ord(pdist[pi])) << 32) | pval[pi];
+            }
+            nk += take;
+            t += uint32_t(take);
+            int n2 = 32;
+            while (n2 < nk) n2 <<= 1;
+            for (int u = nk + lane; u < n2; u += 32) w.keys[u] = ~0ull;
+            __syncwarp();
+            sort_keys(w.keys, n2, lane);
+            nk = min(nk, kKeep);
+            if (t >= uint32_t(nin)) break;
+        }
+        for (int u = lane; u < nk; u += 32) {
+            w.cid[u] = uint32_t(w.keys[u] & 0xffffffffu);
+            w.cd[u] = ord2f(uint32_t(w.keys[u] >> 32));
+        }
+        __syncwarp();
+        const int nr = select_links(rows, stride, d, dp, metric, w.cid, w.cd, nk, Mmax0, heuristic != 0,
+                                    keep_pruned != 0, w, lane);
+        for (int j = lane; j < Mmax0; j += 32) row[j] = j < nr ? w.Rid[j] : kNone;
+        __syncwarp();
+    }
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+hnsw_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(HNSW_ECUDA, std::string("hnsw_build_gpu: ") + what + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" hnsw_status hnsw_build_gpu(const float* data, uint64_t N, uint32_t d, hnsw_metric metric,
+                                      const hnsw_build_params* params, const double* level_u, void* stream,
+                                      void** out_blob, uint64_t* out_bytes) {
+    if (!params || !out_blob || !out_bytes || (N > 0 && (!data || !level_u)))
+        return fail(HNSW_EINVAL, "hnsw_build_gpu: null pointer");
+    const hnsw_build_params& p = *params;
+    if (d == 0 || d > 32u * kMaxDW || N >= (1ull << 31) || p.M == 0 || p.M > p.Mmax || p.M > p.Mmax0 ||
+        p.Mmax0 > 64 || p.Mmax > 64 || !(p.mL > 0) || p.ef_construction == 0 || p.ef_construction > 1024 ||
+        p.extend_candidates || (metric != HNSW_L2SQ && metric != HNSW_COSINE))
+        return fail(HNSW_EINVAL, "hnsw_build_gpu: invalid parameters (d <= 256, efConstruction <= 1024, "
+                                 "no extendCandidates)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // levels (Alg. 1 line 4) and the seed: the first elements and every
+    // element of level >= 1, in id order
+    std::vector<uint8_t> level(N);
+    uint64_t rows = 0;
+    for (uint64_t i = 0; i < N; ++i) {
+        const double u = level_u[i];
+        if (!(u > 0.0 && u <= 1.0)) return fail(HNSW_EINVAL, "hnsw_build_gpu: level_u outside (0,1]");
+        const double lv = std::floor(-std::log(u) * p.mL);
+        if (lv > 255) return fail(HNSW_EINVAL, "hnsw_build_gpu: level above 255");
+        level[i] = uint8_t(lv);
+        rows += level[i];
+    }
+    const uint64_t n_first = std::min<uint64_t>(N, 4096);
+    std::vector<uint32_t> seed, rest;
+    for (uint64_t i = 0; i < N; ++i) (i < n_first || level[i] > 0 ? seed : rest).push_back(uint32_t(i));
+    if (rest.empty()) return hnsw_build(data, N, d, metric, params, level_u, out_blob, out_bytes);
+    // 1. the seed on the host
+    std::vector<float> sdata(seed.size() * size_t(d));
+    std::vector<double> su(seed.size());
+    for (size_t j = 0; j < seed.size(); ++j) {
+        std::memcpy(&sdata[j * d], data + uint64_t(seed[j]) * d, d * 4ull);
+        su[j] = level_u[seed[j]];
+    }
+    void* sblob = nullptr;
+    uint64_t sbytes = 0;
+    hnsw_status st = hnsw_build(sdata.data(), seed.size(), d, metric, params, su.data(), &sblob, &sbytes);
+    if (st != HNSW_OK) return st;
+    BlobHeader sh{};
+    read_header(static_cast<const uint8_t*>(sblob), sbytes, sh);
+    const BlobLayout sl = BlobLayout::of(seed.size(), d, p.Mmax0, p.Mmax, sh.n_upper_rows);
+    // the full blob: all vectors and levels, the seed's links in original ids
+    const BlobLayout lay = BlobLayout::of(N, d, p.Mmax0, p.Mmax, rows);
+    uint8_t* b = static_cast<uint8_t*>(std::calloc(lay.total, 1));
+    if (!b) {
+        hnsw_free_blob(sblob);
+        return fail(HNSW_ENOMEM, "hnsw_build_gpu: blob allocation failed");
+    }
+    const uint8_t* sb = static_cast<const uint8_t*>(sblob);
+    std::memcpy(b + lay.data, data, N * d * 4ull);
+    std::memcpy(b + lay.level, level.data(), N);
+    for (uint64_t i = 0; i < N * p.Mmax0; ++i) wr<uint32_t>(b + lay.nbr0 + 4 * i, kNone);
+    auto map = [&](uint32_t v) { return v == kNone ? kNone : seed[v]; };
+    for (size_t j = 0; j < seed.size(); ++j)
+        for (uint32_t c = 0; c < p.Mmax0; ++c)
+            wr<uint32_t>(b + lay.nbr0 + (uint64_t(seed[j]) * p.Mmax0 + c) * 4,
+                         map(rd<uint32_t>(sb + sl.nbr0 + (uint64_t(j) * p.Mmax0 + c) * 4)));
+    // upper rows are element-major; the seed holds every element of level >= 1
+    // in id order, so its rows are already in the full graph's order
+    for (uint64_t r = 0; r < sh.n_upper_rows * p.Mmax; ++r)
+        wr<uint32_t>(b + lay.nbrU + r * 4, map(rd<uint32_t>(sb + sl.nbrU + r * 4)));
+    BlobHeader h = sh;
+    h.N = N;
+    h.ep = map(sh.ep);
+    h.n_upper_rows = rows;
+    hnsw_free_blob(sblob);
+    auto finish_header = [&]() {
+        h.checksum = fnv1a64(b + 128, lay.total - 128);
+        write_header(b, h);
+    };
+    finish_header();
+    // 2. layer-0 insertion of the rest on the GPU
+    hnsw_index* ix = nullptr;
+    st = hnsw_upload_index(b, lay.total, HNSW_F32, 0, stream, &ix);
+    if (st != HNSW_OK) {
+        std::free(b);
+        return st;
+    }
+    struct IxGuard {
+        hnsw_index* ix;
+        ~IxGuard() { hnsw_free_index(ix); }
+    } ixg{ix};
+    const DevIndex& D = ix->dev;
+    const float* drows = reinterpret_cast<const float*>(D.vec);
+    const uint32_t stride = D.row_chunks * 4, dp = D.row_chunks * 4, s0 = D.s0;
+    uint32_t* nbr0 = static_cast<uint32_t*>(ix->d_nbr0);
+    const int efc = int(p.ef_construction), M = int(p.M), Mmax0 = int(p.Mmax0);
+    const uint32_t Bmax = uint32_t(std::min<uint64_t>(32768, std::max<uint64_t>(64, rest.size())));
+    DevBuf dbid, dq, rid, rdist, pkey, pval, pdist, skey, sidx, idx, seg, nseg, work, tmp;
+    size_t tmp_bytes = 0;
+    const uint32_t npair_max = Bmax * uint32_t(M);
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, static_cast<uint32_t*>(nullptr),
+                                    static_cast<uint32_t*>(nullptr), static_cast<uint32_t*>(nullptr),
+                                    static_cast<uint32_t*>(nullptr), int(npair_max), 0, 32, s);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](DevBuf& x, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(&x.p, bytes ? bytes : 16);
+    };
+    alloc(dbid, size_t(rest.size()) * 4);
+    alloc(dq, size_t(Bmax) * d * 4);
+    alloc(rid, size_t(Bmax) * efc * 4);
+    alloc(rdist, size_t(Bmax) * efc * 4);
+    alloc(pkey, size_t(npair_max) * 4);
+    alloc(pval, size_t(npair_max) * 4);
+    alloc(pdist, size_t(npair_max) * 4);
+    alloc(skey, size_t(npair_max) * 4);
+    alloc(sidx, size_t(npair_max) * 4);
+    alloc(idx, size_t(npair_max) * 4);
+    alloc(seg, size_t(npair_max) * 4);
+    alloc(nseg, 16);
+    alloc(work, 16);
+    alloc(tmp, tmp_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        std::free(b);
+        return fail(HNSW_ENOMEM, "hnsw_build_gpu: device buffers");
+    }
+    std::vector<uint32_t> iota(npair_max);
+    for (uint32_t i = 0; i < npair_max; ++i) iota[i] = i;
+    if ((e = cudaMemcpyAsync(idx.p, iota.data(), size_t(npair_max) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dbid.p, rest.data(), rest.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+        std::free(b);
+        return cuda_fail(e, "copy");
+    }
+    // warps per block: as many (up to kWarps) as the shared memory allows
+    auto warps_for = [](size_t per_warp) {
+        int nw = kWarps;
+        while (nw > 1 && size_t(nw) * per_warp > 227 * 1024) --nw;
+        return nw;
+    };
+    const int fw_w = warps_for(warp_smem_bytes(M, dp, efc)), rv_w = warps_for(warp_smem_bytes(Mmax0, dp, kKeep));
+    const size_t fw_smem = size_t(fw_w) * warp_smem_bytes(M, dp, efc);
+    const size_t rv_smem = size_t(rv_w) * warp_smem_bytes(Mmax0, dp, kKeep);
+    if (fw_smem > 227 * 1024 || rv_smem > 227 * 1024) {
+        std::free(b);
+        return fail(HNSW_EINVAL, "hnsw_build_gpu: dimension too large for the selection kernels");
+    }
+    cudaFuncSetAttribute(select_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fw_smem));
+    cudaFuncSetAttribute(link_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rv_smem));
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    hnsw_search_params sp{};
+    sp.k = efc;
+    sp.ef = efc;
+    uint64_t inserted = seed.size();
+    for (size_t pos = 0; pos < rest.size();) {
+        const uint32_t B = uint32_t(std::min<uint64_t>(
+            {uint64_t(Bmax), uint64_t(rest.size() - pos), std::max<uint64_t>(64, inserted / 16)}));
+        const uint32_t* bids = static_cast<const uint32_t*>(dbid.p) + pos;
+        const uint64_t nq = uint64_t(B) * d;
+        gather_rows<<<unsigned((nq + 255) / 256), 256, 0, s>>>(drows, stride, d, bids, B, static_cast<float*>(dq.p));
+        if ((e = cudaMemsetAsync(work.p, 0, 8, s)) != cudaSuccess) break;
+        st = launch_search(ix, sp, static_cast<const float*>(dq.p), B, static_cast<uint32_t*>(rid.p),
+                           static_cast<float*>(rdist.p), nullptr, s, static_cast<uint32_t*>(work.p), nullptr);
+        if (st != HNSW_OK) break;
+        select_forward<<<(B + fw_w - 1) / fw_w, fw_w * 32, fw_smem, s>>>(
+            drows, stride, d, dp, int(metric), bids, B, static_cast<const uint32_t*>(rid.p),
+            static_cast<const float*>(rdist.p), efc, M, p.heuristic, p.keep_pruned, nbr0, s0,
+            static_cast<uint32_t*>(pkey.p), static_cast<uint32_t*>(pval.p), static_cast<float*>(pdist.p));
+        const uint32_t np = B * uint32_t(M);
+        size_t tb = tmp_bytes;
+        if ((e = cub::DeviceRadixSort::SortPairs(tmp.p, tb, static_cast<const uint32_t*>(pkey.p),
+                                                 static_cast<uint32_t*>(skey.p), static_cast<const uint32_t*>(idx.p),
+                                                 static_cast<uint32_t*>(sidx.p), int(np), 0, 32, s)) != cudaSuccess)
+            break;
+        if ((e = cudaMemsetAsync(nseg.p, 0, 4, s)) != cudaSuccess) break;
+        mark_segments<<<(np + 255) / 256, 256, 0, s>>>(static_cast<const uint32_t*>(skey.p), np,
+                                                      static_cast<uint32_t*>(seg.p), static_cast<uint32_t*>(nseg.p));
+        link_reverse<<<unsigned(sms) * 4, rv_w * 32, rv_smem, s>>>(
+            drows, stride, d, dp, int(metric), static_cast<const uint32_t*>(skey.p),
+            static_cast<const uint32_t*>(sidx.p), np, static_cast<const uint32_t*>(seg.p),
+            static_cast<const uint32_t*>(nseg.p), static_cast<const uint32_t*>(pval.p),
+            static_cast<const float*>(pdist.p), nbr0, s0, Mmax0, p.heuristic, p.keep_pruned);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        pos += B;
+        inserted += B;
+    }
+    if (st != HNSW_OK || e != cudaSuccess) {
+        std::free(b);
+        return st != HNSW_OK ? st : cuda_fail(e, "batch");
+    }
+    // 3. the final layer 0 back into the blob
+    std::vector<uint32_t> h0(N * size_t(s0));
+    if ((e = cudaMemcpyAsync(h0.data(), nbr0, h0.size() * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        std::free(b);
+        return cuda_fail(e, "layer 0 copy");
+    }
+    for (uint64_t i = 0; i < N; ++i)
+        for (uint32_t c = 0; c < p.Mmax0; ++c) wr<uint32_t>(b + lay.nbr0 + (i * p.Mmax0 + c) * 4, h0[i * s0 + c]);
+    finish_header();
+    *out_blob = b;
+    *out_bytes = lay.total;
+    return HNSW_OK;
+}

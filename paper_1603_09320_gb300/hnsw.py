@@ -92,6 +92,8 @@ def lib():
         sig = {
             "hnsw_build": (i32, [vp, u64, u32, i32, C.POINTER(BuildParams), vp, C.POINTER(vp), C.POINTER(u64)]),
             "hnsw_free_blob": (None, [vp]),
+            "hnsw_build_gpu": (i32, [vp, u64, u32, i32, C.POINTER(BuildParams), vp, vp, C.POINTER(vp),
+                                     C.POINTER(u64)]),
             "hnsw_upload_index": (i32, [vp, u64, i32, i32, vp, C.POINTER(vp)]),
             "hnsw_free_index": (i32, [vp]),
             "hnsw_get_index_info": (i32, [vp, C.POINTER(IndexInfo)]),
@@ -172,6 +174,30 @@ def build_graph(data: np.ndarray, level_u: np.ndarray, metric: int = L2SQ, M: in
     nbytes = C.c_uint64()
     _check(lib().hnsw_build(data.ctypes.data, N, d, metric, C.byref(p), u.ctypes.data, C.byref(out),
                             C.byref(nbytes)))
+    try:
+        return C.string_at(out.value, nbytes.value)
+    finally:
+        lib().hnsw_free_blob(out)
+
+
+def build_graph_gpu(data: np.ndarray, level_u: np.ndarray, metric: int = L2SQ, M: int = 16,
+                    Mmax: int | None = None, Mmax0: int | None = None, ef_construction: int = 200,
+                    mL: float | None = None, heuristic: bool = True, keep_pruned: bool = False,
+                    n_threads: int = 0, stream=None) -> bytes:
+    """hnsw_build_gpu: the seed (elements of level >= 1 and the first 4,096)
+    built on the host, the other elements inserted into layer 0 on the current
+    CUDA device in batches; returns an HNSWGB01 blob."""
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    u = np.ascontiguousarray(level_u, dtype=np.float64)
+    N, d = data.shape
+    if u.shape != (N,):
+        raise ValueError("level_u must hold one value per element")
+    p = BuildParams(M, M if Mmax is None else Mmax, 2 * M if Mmax0 is None else Mmax0, ef_construction,
+                    1.0 / np.log(M) if mL is None else mL, int(heuristic), 0, int(keep_pruned), n_threads)
+    out = C.c_void_p()
+    nbytes = C.c_uint64()
+    _check(lib().hnsw_build_gpu(data.ctypes.data, N, d, metric, C.byref(p), u.ctypes.data, _stream_ptr(stream),
+                                C.byref(out), C.byref(nbytes)))
     try:
         return C.string_at(out.value, nbytes.value)
     finally:

@@ -74,6 +74,29 @@ def test_builder_multithreaded_graph_is_valid(H, oracle):
     assert recall(ids, bi) > 0.95
 
 
+def test_builder_multithreaded_keeps_m_links(H, oracle):
+    # Alg. 3 keeps M links whenever it has M candidates, and a shrink keeps
+    # Mmax0 >= M: the sequential graph has no element below M links, and the
+    # concurrent build (after its sequential start) must not have any either
+    p = synth.params("tiny")
+    X = synth.base("tiny", 6000)
+    u = synth.level_uniforms("tiny", 6000)
+    b = H.build_graph(X, u, M=p["M"], ef_construction=p["efC"], heuristic=False, n_threads=8)
+    g = oracle.Graph.from_blob(b)
+    assert min(len(g.neighbors(i, 0)) for i in range(6000)) >= p["M"]
+
+
+def test_gpu_builder_rejects_bad_params_without_gpu(H):
+    # parameter checks come before any CUDA call
+    X = synth.base("tiny", 10)
+    u = np.full(10, 0.5)
+    for kw in (dict(M=8, Mmax=4), dict(M=8, ef_construction=2000), dict(M=8, mL=-1.0)):
+        with pytest.raises(H.HnswError):
+            H.build_graph_gpu(X, u, **kw)
+    with pytest.raises(H.HnswError):
+        H.build_graph_gpu(np.zeros((10, 300), np.float32), u, M=8)
+
+
 def test_builder_rejects_bad_params(H):
     X = synth.base("tiny", 10)
     with pytest.raises(H.HnswError):

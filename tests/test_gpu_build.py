@@ -1,0 +1,160 @@
+"""hnsw_build_gpu: the seed built on the host, layer 0 of the other elements
+built on the GPU in batches.  Parity with sequential insertion is unpinned
+(batch-parallel insertion); what is pinned:
+
+* the upper layers and the enter point equal the oracle's Alg. 1 run over the
+  seed (every element of level >= 1 and the first 4,096, in id order), since
+  layers >= 1 only ever involve elements of level >= 1;
+* the graph passes the oracle's validating loader and the library's upload
+  (ids in range, no self or duplicate links, caps, links to present elements);
+* every element has links, and as many elements are reachable from the
+  enter point along layer-0 links as in the oracle's sequential graph (Alg. 1
+  itself leaves a few unreachable: links are directed and a shrink can drop
+  an element's last in-link -- 9 of 10,000 in the tiny configuration), and
+  the recall of the search equals the host-built graph's within a small
+  margin.
+"""
+import numpy as np
+import pytest
+
+from paper_1603_09320_gb300 import synth
+from _graphs import recall
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1603_09320_gb300 import build, hnsw
+    build.build()
+    return hnsw
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    return oracle
+
+
+def seed_of(levels, n_first=4096):
+    return np.array([i for i in range(len(levels)) if i < n_first or levels[i] > 0], dtype=np.int64)
+
+
+def layer0_reachable(g):
+    seen = np.zeros(g.N, dtype=bool)
+    stack = [g.enter_point]
+    seen[g.enter_point] = True
+    while stack:
+        i = stack.pop()
+        for j in g.neighbors(i, 0):
+            if not seen[j]:
+                seen[j] = True
+                stack.append(j)
+    return int(seen.sum())
+
+
+def gpu_recall(H, blob, Q, gt, k, ef):
+    import torch
+    ix = H.Index(blob, "f32")
+    ids, _ = ix.search(torch.from_numpy(Q).cuda(), k, ef)
+    torch.cuda.synchronize()
+    out = ids.cpu().numpy().view(np.uint32)
+    ix.close()
+    return recall(out, gt)
+
+
+def test_tiny_structure_and_exact_upper_layers(H, O):
+    p = synth.params("tiny")
+    N = 10_000
+    X = synth.base("tiny", N)
+    u = synth.level_uniforms("tiny", N)
+    blob = H.build_graph_gpu(X, u, M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], ef_construction=p["efC"],
+                             n_threads=1)
+    g = O.Graph.from_blob(blob)  # validating loader
+    lv = g.levels()
+    seed = seed_of(lv)
+    assert len(seed) < N  # part of layer 0 was built on the GPU
+    # the seed's upper layers: Alg. 1 over the seed in id order, exactly
+    gs = O.Graph.build(X[seed], u[seed], **p)
+    assert g.enter_point == seed[gs.enter_point]
+    assert g.max_level == gs.max_level
+    for j in range(len(seed)):
+        for lc in range(1, gs.level(j) + 1):
+            assert g.neighbors(int(seed[j]), lc) == [int(seed[x]) for x in gs.neighbors(j, lc)]
+    # caps, no self or duplicate links, every element linked
+    for i in range(N):
+        nb = g.neighbors(i, 0)
+        assert 1 <= len(nb) <= p["Mmax0"]
+        assert i not in nb and len(set(nb)) == len(nb)
+    from _graphs import oracle_graph
+    assert layer0_reachable(g) >= layer0_reachable(oracle_graph("tiny", N)[0])
+    # the library accepts it too
+    ix = H.Index(blob, "f32")
+    ix.close()
+
+
+def test_tiny_recall_matches_host_build(H, O):
+    p = synth.params("tiny")
+    N = 10_000
+    X = synth.base("tiny", N)
+    u = synth.level_uniforms("tiny", N)
+    Q = synth.queries("tiny", 500)
+    gt, _ = O.brute_force(X, Q, 10)
+    kw = dict(M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], ef_construction=p["efC"])
+    bg = H.build_graph_gpu(X, u, **kw)
+    bh = H.build_graph(X, u, **kw)
+    for ef in (16, 32, 64):
+        rg, rh = gpu_recall(H, bg, Q, gt, 10, ef), gpu_recall(H, bh, Q, gt, 10, ef)
+        assert rg >= rh - 0.015, (ef, rg, rh)
+
+
+@pytest.mark.parametrize("heuristic,keep_pruned", [(False, False), (True, True)])
+def test_selection_variants_are_valid(H, O, heuristic, keep_pruned):
+    p = synth.params("tiny")
+    N = 6_000
+    X = synth.base("tiny", N)
+    u = synth.level_uniforms("tiny", N)
+    blob = H.build_graph_gpu(X, u, M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], ef_construction=p["efC"],
+                             heuristic=heuristic, keep_pruned=keep_pruned, n_threads=1)
+    g = O.Graph.from_blob(blob)
+    degs = [len(g.neighbors(i, 0)) for i in range(N)]
+    assert min(degs) >= 1 and max(degs) <= p["Mmax0"]
+    # Alg. 3 and Alg. 4 with keepPrunedConnections keep M links whenever they
+    # have M candidates, and lists only shrink to Mmax0 >= M
+    assert min(degs) >= p["M"]
+    # as connected as the oracle's sequential graph with the same selection
+    # (Alg. 3 leaves more elements unreachable than Alg. 4)
+    go = O.Graph.build(X, u, heuristic=heuristic, keep_pruned=keep_pruned, **p)
+    assert layer0_reachable(g) >= layer0_reachable(go) - 0.002 * N
+
+
+def test_sift_shaped_recall_matches_host_build(H, O):
+    p = synth.params("sift")
+    N = 100_000
+    X = synth.base("sift", N)
+    u = synth.level_uniforms("sift", N)
+    Q = synth.queries("sift", 500)
+    gt, _ = O.brute_force(X, Q, 10)
+    kw = dict(M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], ef_construction=p["efC"])
+    bg = H.build_graph_gpu(X, u, **kw)
+    bh = H.build_graph(X, u, **kw)
+    g = O.Graph.from_blob(bg)
+    assert layer0_reachable(g) >= 0.998 * N
+    for ef in (32, 64):
+        rg, rh = gpu_recall(H, bg, Q, gt, 10, ef), gpu_recall(H, bh, Q, gt, 10, ef)
+        assert rg >= rh - 0.01, (ef, rg, rh)
+
+
+def test_cosine_build_is_valid(H, O):
+    p = synth.params("glove")
+    N = 20_000
+    X = synth.base("glove", N)
+    u = synth.level_uniforms("glove", N)
+    Q = synth.queries("glove", 300)
+    blob = H.build_graph_gpu(X, u, metric=H.COSINE, M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], ef_construction=200)
+    g = O.Graph.from_blob(blob)
+    assert layer0_reachable(g) >= 0.998 * N
+    gt, _ = O.brute_force(X, Q, 10, metric=1)
+    assert gpu_recall(H, blob, Q, gt, 10, 128) > 0.9
