@@ -98,6 +98,8 @@ def parse():
                     help="serving mix: SIFT-shaped 1M and GloVe-shaped 1.2M indexes resident, Poisson requests")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-rate", type=float, default=20_000.0, help="mean requests per second")
+    ap.add_argument("--build-compare", action="store_true",
+                    help="graph construction: hnsw_build_gpu against the host builder on the bench workload")
     ap.add_argument("--profile-form", default=None,
                     help="profiling run: upload only this form and launch the search --profile-launches times")
     ap.add_argument("--profile-ef", type=int, default=64)
@@ -561,6 +563,8 @@ def main():
         return reference_arm(args, rank, world, log)
     if args.serving:
         return serving_bench(args, log)
+    if args.build_compare:
+        return build_compare(args, log)
 
     import torch
     torch.cuda.set_device(local)
@@ -697,6 +701,44 @@ def main():
     }
     out["cpu_baseline"]["recall_at_10"] = cpu["recall"]
     out["cpu_baseline"]["oracle_n_dist_mean"] = cpu["n_dist_mean"]
+    print(json.dumps(out), flush=True)
+
+
+def build_compare(args, log):
+    """Construction of the bench graph (SIFT-shaped 1M x 128, M=16, Mmax0=32,
+    efC=200) by hnsw_build_gpu and by the host builder on all host cores;
+    recall@10 of the search on each graph over 2,000 of the queries."""
+    import torch
+    from paper_1603_09320_gb300 import build as B
+    from paper_1603_09320_gb300 import hnsw, synth
+    B.build()
+    X, Q, u = workload(args)
+    p = synth.params("sift")
+    kw = dict(M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], ef_construction=p["efC"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bg = hnsw.build_graph_gpu(X, u, **kw)
+    t_gpu = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bh = hnsw.build_graph(X, u, **kw)
+    t_host = time.perf_counter() - t0
+    Qs = Q[:2000]
+    gt = ground_truth(X, Qs, args.k, torch.device("cuda", torch.cuda.current_device()))
+    q = torch.from_numpy(Qs).cuda()
+    out = {"metric": "graph construction seconds and recall@10 of the search on the graph",
+           "data": "synthetic", "n_gpus": 1,
+           "config": {"workload": f"SIFT-shaped {args.n_base}x{X.shape[1]}, M=16 Mmax0=32 efC=200; "
+                                  f"recall over {Qs.shape[0]} queries", "host_threads": os.cpu_count(),
+                      "cpu_model": cpu_model()},
+           "gpu_build_s": round(t_gpu, 3), "host_build_s": round(t_host, 3), "recall": {}}
+    for name, b in (("gpu", bg), ("host", bh)):
+        ix = hnsw.Index(b, "f32")
+        for ef in (32, 48, 52, 64):
+            ids, _ = ix.search(q, args.k, ef)
+            torch.cuda.synchronize()
+            out["recall"][f"{name}@{ef}"] = round(recall_at(ids.cpu().numpy().view(np.uint32), gt), 5)
+        ix.close()
+    log(f"build compare: {out}")
     print(json.dumps(out), flush=True)
 
 

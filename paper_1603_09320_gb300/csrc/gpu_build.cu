@@ -411,7 +411,7 @@ extern "C" hnsw_status hnsw_build_gpu(const float* data, uint64_t N, uint32_t d,
     const uint8_t* sb = static_cast<const uint8_t*>(sblob);
     std::memcpy(b + lay.data, data, N * d * 4ull);
     std::memcpy(b + lay.level, level.data(), N);
-    for (uint64_t i = 0; i < N * p.Mmax0; ++i) wr<uint32_t>(b + lay.nbr0 + 4 * i, kNone);
+    std::memset(b + lay.nbr0, 0xFF, N * p.Mmax0 * 4ull);  // every slot kNone
     auto map = [&](uint32_t v) { return v == kNone ? kNone : seed[v]; };
     for (size_t j = 0; j < seed.size(); ++j)
         for (uint32_t c = 0; c < p.Mmax0; ++c)
