@@ -98,6 +98,10 @@ def parse():
                     help="serving mix: SIFT-shaped 1M and GloVe-shaped 1.2M indexes resident, Poisson requests")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-rate", type=float, default=20_000.0, help="mean requests per second")
+    ap.add_argument("--ablation", action="store_true",
+                    help="selection ablation: Alg. 3 vs Alg. 4 (with and without extendCandidates) on "
+                         "clustered low-d data")
+    ap.add_argument("--ablation-n", type=int, default=1_000_000)
     ap.add_argument("--build-compare", action="store_true",
                     help="graph construction: hnsw_build_gpu against the host builder on the bench workload")
     ap.add_argument("--profile-form", default=None,
@@ -565,6 +569,8 @@ def main():
         return serving_bench(args, log)
     if args.build_compare:
         return build_compare(args, log)
+    if args.ablation:
+        return ablation(args, log)
 
     import torch
     torch.cuda.set_device(local)
@@ -739,6 +745,75 @@ def build_compare(args, log):
             out["recall"][f"{name}@{ef}"] = round(recall_at(ids.cpu().numpy().view(np.uint32), gt), 5)
         ix.close()
     log(f"build compare: {out}")
+    print(json.dumps(out), flush=True)
+
+
+def exact_knn_direct(X, Q, k, device):
+    """Exact k-NN on the GPU with direct differences (no |x|^2 - 2 x.q
+    expansion, which cancels on tight clusters): a shortlist of 32 per query
+    in fp32, rescored in fp64 on the host by key (distance, id)."""
+    import torch
+    Xd = torch.from_numpy(X).to(device)
+    out = np.zeros((Q.shape[0], k), dtype=np.int64)
+    for s0 in range(0, Q.shape[0], 16):  # 16 x N x d floats at a time
+        q = torch.from_numpy(Q[s0:s0 + 16]).to(device)
+        d = ((Xd[None, :, :] - q[:, None, :]) ** 2).sum(2)
+        cand = torch.topk(d, 32, dim=1, largest=False).indices.cpu().numpy()
+        for i in range(cand.shape[0]):
+            c = cand[i]
+            ex = ((X[c].astype(np.float64) - Q[s0 + i].astype(np.float64)) ** 2).sum(1)
+            out[s0 + i] = c[np.lexsort((c, ex))[:k]]
+    del Xd
+    torch.cuda.empty_cache()
+    return out
+
+
+def ablation(args, log):
+    """The selection of neighbours on clustered low-dimensional data (the
+    setting where the paper motivates Alg. 4, Section 4; Fig. 7): graphs of
+    the first args.ablation_n low-d vectors (d=8, 95% in 10,000 clusters of
+    sigma 1e-3, 5% uniform; M=12, Mmax0=24, efC=100) built by the host
+    builder with Alg. 3, Alg. 4, and Alg. 4 with extendCandidates; for each,
+    recall@10 of the GPU search over 10,000 queries (90% cluster-drawn), the
+    distance evaluations per query and the time of one 10,000-query batch."""
+    import torch
+    from paper_1603_09320_gb300 import build as B
+    from paper_1603_09320_gb300 import hnsw, synth
+    B.build()
+    n = args.ablation_n
+    X = synth.base("lowd", n)
+    u = synth.level_uniforms("lowd", n)
+    Q = synth.queries("lowd", 10_000)
+    p = synth.params("lowd")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gt = exact_knn_direct(X, Q, 10, dev)
+    q = torch.from_numpy(Q).to(dev)
+    ids = torch.empty((Q.shape[0], 10), dtype=torch.int32, device=dev)
+    ds = torch.empty((Q.shape[0], 10), dtype=torch.float32, device=dev)
+    st = torch.empty((Q.shape[0], 4), dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    variants = {"alg3_simple": dict(heuristic=False), "alg4_heuristic": dict(heuristic=True),
+                "alg4_extend_candidates": dict(heuristic=True, extend_candidates=True)}
+    out = {"metric": "recall@10, distance evaluations and batch time per selection rule",
+           "data": "synthetic", "n_gpus": 1,
+           "config": {"workload": f"clustered low-d {n}x8 (95% in 10,000 clusters, sigma 1e-3; 5% uniform), "
+                                  "M=12 Mmax0=24 efC=100, 10,000 queries (90% cluster-drawn), k=10"},
+           "variants": {}}
+    for name, kw in variants.items():
+        t0 = time.perf_counter()
+        blob = hnsw.build_graph(X, u, M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], ef_construction=p["efC"], **kw)
+        tb = time.perf_counter() - t0
+        ix = hnsw.Index(blob, "f32")
+        rows = []
+        for ef in (10, 20, 40, 80, 160):
+            setting = {"ef": ef, "rerank": False}
+            t, stv = time_form(args, ix, setting, (q, ids, ds, st), 5, 2, flush)
+            r = recall_at(ids.cpu().numpy().view(np.uint32), gt)
+            rows.append({"ef": ef, "recall_at_10": round(r, 5), "ms_per_batch": round(statistics.mean(t), 4),
+                         "n_eval": round(float(stv[:, 0].mean()), 1)})
+        ix.close()
+        out["variants"][name] = {"build_s": round(tb, 2), "sweep": rows}
+        log(f"ablation {name}: {rows}")
     print(json.dumps(out), flush=True)
 
 
