@@ -126,6 +126,17 @@ hnsw_status hnsw_build_gpu(const float* data, uint64_t N, uint32_t d, hnsw_metri
  *     u32 nbrU[n_upper_rows][Mmax] (element-major, layers 1..level[i]);
  *   lists hold their valid ids first, then 0xFFFFFFFF. */
 
+/* Graph files.  hnsw_save_blob validates the blob (as hnsw_upload_index does)
+ * and writes its bytes to `path` through a temporary file `path`.tmp renamed
+ * over `path`, so that an interrupted save leaves no partial graph under that
+ * name.  hnsw_load_blob reads and validates a file; on success *out_blob is a
+ * library-allocated blob of *out_bytes bytes, freed with hnsw_free_blob.
+ * Errors: HNSW_EINVAL (null arguments, the file cannot be opened, created
+ * or written), HNSW_ECORRUPT (failed validation, short or empty file),
+ * HNSW_ENOMEM. */
+hnsw_status hnsw_save_blob(const void* blob, uint64_t blob_bytes, const char* path);
+hnsw_status hnsw_load_blob(const char* path, void** out_blob, uint64_t* out_bytes);
+
 /* ------------------------------------------------------------------------ */
 /* Device index                                                              */
 /* ------------------------------------------------------------------------ */

@@ -1,4 +1,9 @@
-// blob.cpp -- error reporting and validation of "HNSWGB01" graph blobs.
+// blob.cpp -- error reporting, validation of "HNSWGB01" graph blobs, and
+// their files.
+#include <cerrno>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -74,3 +79,58 @@ hnsw_status validate_blob(const uint8_t* b, uint64_t bytes, BlobHeader& h, BlobL
 
 extern "C" const char* hnsw_last_error(void) { return hnswgb::g_last_error.c_str(); }
 extern "C" int hnsw_abi_version(void) { return HNSW_ABI_VERSION; }
+
+using namespace hnswgb;
+
+extern "C" hnsw_status hnsw_save_blob(const void* blob, uint64_t bytes, const char* path) {
+    if (!blob || !path) return fail(HNSW_EINVAL, "hnsw_save_blob: null argument");
+    BlobHeader h{};
+    BlobLayout lay{};
+    std::vector<uint32_t> upoff;
+    hnsw_status st = validate_blob(static_cast<const uint8_t*>(blob), bytes, h, lay, upoff);
+    if (st != HNSW_OK) return st;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail(HNSW_EINVAL, "hnsw_save_blob: cannot create " + tmp + ": " + std::strerror(errno));
+    const bool ok = std::fwrite(blob, 1, bytes, f) == bytes;
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return fail(HNSW_EINVAL, std::string("hnsw_save_blob: write failed: ") + std::strerror(errno));
+    }
+    return HNSW_OK;
+}
+
+extern "C" hnsw_status hnsw_load_blob(const char* path, void** out_blob, uint64_t* out_bytes) {
+    if (!path || !out_blob || !out_bytes) return fail(HNSW_EINVAL, "hnsw_load_blob: null argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(HNSW_EINVAL, std::string("hnsw_load_blob: cannot open ") + path + ": " + std::strerror(errno));
+    uint64_t bytes = 0;
+    if (std::fseek(f, 0, SEEK_END) == 0) {
+        const long n = std::ftell(f);
+        bytes = n > 0 ? uint64_t(n) : 0;
+    }
+    std::rewind(f);
+    uint8_t* b = bytes ? static_cast<uint8_t*>(std::malloc(bytes)) : nullptr;
+    if (bytes && !b) {
+        std::fclose(f);
+        return fail(HNSW_ENOMEM, "hnsw_load_blob: out of host memory");
+    }
+    const bool ok = bytes > 0 && std::fread(b, 1, bytes, f) == bytes;
+    std::fclose(f);
+    if (!ok) {
+        std::free(b);
+        return fail(HNSW_ECORRUPT, std::string("hnsw_load_blob: short or empty file ") + path);
+    }
+    BlobHeader h{};
+    BlobLayout lay{};
+    std::vector<uint32_t> upoff;
+    hnsw_status st = validate_blob(b, bytes, h, lay, upoff);
+    if (st != HNSW_OK) {
+        std::free(b);
+        return st;
+    }
+    *out_blob = b;
+    *out_bytes = bytes;
+    return HNSW_OK;
+}

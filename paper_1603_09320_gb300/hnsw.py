@@ -92,6 +92,8 @@ def lib():
         sig = {
             "hnsw_build": (i32, [vp, u64, u32, i32, C.POINTER(BuildParams), vp, C.POINTER(vp), C.POINTER(u64)]),
             "hnsw_free_blob": (None, [vp]),
+            "hnsw_save_blob": (i32, [vp, u64, C.c_char_p]),
+            "hnsw_load_blob": (i32, [C.c_char_p, C.POINTER(vp), C.POINTER(u64)]),
             "hnsw_build_gpu": (i32, [vp, u64, u32, i32, C.POINTER(BuildParams), vp, vp, C.POINTER(vp),
                                      C.POINTER(u64)]),
             "hnsw_upload_index": (i32, [vp, u64, i32, i32, vp, C.POINTER(vp)]),
@@ -174,6 +176,23 @@ def build_graph(data: np.ndarray, level_u: np.ndarray, metric: int = L2SQ, M: in
     nbytes = C.c_uint64()
     _check(lib().hnsw_build(data.ctypes.data, N, d, metric, C.byref(p), u.ctypes.data, C.byref(out),
                             C.byref(nbytes)))
+    try:
+        return C.string_at(out.value, nbytes.value)
+    finally:
+        lib().hnsw_free_blob(out)
+
+
+def save_graph(blob: bytes, path: str) -> None:
+    """hnsw_save_blob: validates the blob and writes it to `path`."""
+    buf = np.frombuffer(blob, dtype=np.uint8)
+    _check(lib().hnsw_save_blob(buf.ctypes.data, buf.size, os.fsencode(path)))
+
+
+def load_graph(path: str) -> bytes:
+    """hnsw_load_blob: reads and validates a graph file."""
+    out = C.c_void_p()
+    nbytes = C.c_uint64()
+    _check(lib().hnsw_load_blob(os.fsencode(path), C.byref(out), C.byref(nbytes)))
     try:
         return C.string_at(out.value, nbytes.value)
     finally:

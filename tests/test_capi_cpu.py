@@ -86,6 +86,34 @@ def test_builder_multithreaded_keeps_m_links(H, oracle):
     assert min(len(g.neighbors(i, 0)) for i in range(6000)) >= p["M"]
 
 
+def test_graph_file_round_trip_and_rejections(H, oracle, tmp_path):
+    p = synth.params("tiny")
+    X = synth.base("tiny", 2000)
+    u = synth.level_uniforms("tiny", 2000)
+    b = H.build_graph(X, u, M=p["M"], ef_construction=p["efC"], n_threads=1)
+    path = str(tmp_path / "g.hnsw")
+    H.save_graph(b, path)
+    assert H.load_graph(path) == b
+    assert not (tmp_path / "g.hnsw.tmp").exists()
+    # the loaded graph is the oracle's own graph (same bytes as its blob)
+    assert oracle.Graph.from_blob(H.load_graph(path)).to_blob() == b
+    # a flipped payload byte fails the checksum; a truncated file its size
+    bad = bytearray(b)
+    bad[200] ^= 1
+    (tmp_path / "bad.hnsw").write_bytes(bytes(bad))
+    with pytest.raises(H.HnswError):
+        H.load_graph(str(tmp_path / "bad.hnsw"))
+    (tmp_path / "short.hnsw").write_bytes(b[:-16])
+    with pytest.raises(H.HnswError):
+        H.load_graph(str(tmp_path / "short.hnsw"))
+    with pytest.raises(H.HnswError):
+        H.load_graph(str(tmp_path / "missing.hnsw"))
+    # an invalid blob is not written
+    with pytest.raises(H.HnswError):
+        H.save_graph(bytes(bad), str(tmp_path / "never.hnsw"))
+    assert not (tmp_path / "never.hnsw").exists()
+
+
 def test_gpu_builder_rejects_bad_params_without_gpu(H):
     # parameter checks come before any CUDA call
     X = synth.base("tiny", 10)
