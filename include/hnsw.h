@@ -156,6 +156,46 @@ hnsw_status hnsw_upload_index(const void* graph_blob, uint64_t blob_bytes, hnsw_
 
 hnsw_status hnsw_free_index(hnsw_index* index);
 
+/* ------------------------------------------------------------------------ */
+/* Incremental insertion into a resident index (continuous indexing; Alg. 1) */
+/* ------------------------------------------------------------------------ */
+/* Reserves room for `capacity` elements (>= the current count, < 2^31) and
+ * the upper-layer rows they will need (expected 1/(M-1) per element, twice
+ * that reserved, plus 1,024): the device arrays are reallocated and the
+ * adjacency is kept in two versions from then on.  Synchronises the device;
+ * not to be called while other calls on the index are running.
+ * Errors: HNSW_EINVAL, HNSW_ENOMEM, HNSW_ECUDA. */
+hnsw_status hnsw_reserve(hnsw_index* index, uint64_t capacity, void* stream);
+
+/* Inserts n elements into a resident index as Alg. 1 does, with the graph's
+ * own parameters (M, Mmax, Mmax0, efConstruction, mL, selection flags from
+ * its header): ids count..count+n-1 in order, vectors data[n][d] (host or
+ * device memory; unit-normalised for COSINE), level_u[n] host doubles in
+ * (0,1] (level = floor(-ln u * mL)).  The new elements of level >= 1 are
+ * linked into layer 0 first (searching through the existing upper layers),
+ * then into their upper layers one at a time in id order (a new top level
+ * makes the element the enter point), then the elements of level 0 are
+ * linked into layer 0 in batches of at most 1/16 of the elements present;
+ * elements of one batch do not search one another (see hnsw_build_gpu).
+ * Concurrency: searches may be issued on other streams and host threads
+ * during the call.  The call first synchronises the device (so that no
+ * search still reads the adjacency version it is about to overwrite), writes
+ * a copy of the adjacency, and publishes it when its work is done: a search
+ * launched before the publication sees the graph without the new elements,
+ * a search launched after it sees all of them.  Inserts on one index are
+ * serialised.  Needs the fp32 vectors (F32 storage, or keep_fp32_for_rerank)
+ * and a non-empty index built by hnsw_build or hnsw_build_gpu without
+ * extendCandidates.  Work is issued on `stream`, synchronised before return.
+ * Errors: HNSW_EINVAL (null pointers, no reserved capacity, capacity or
+ * upper rows exceeded, level_u outside (0,1], d > 256, fp32 vectors absent),
+ * HNSW_ENOMEM, HNSW_ECUDA. */
+hnsw_status hnsw_insert(hnsw_index* index, const float* data, uint64_t n, const double* level_u, void* stream);
+
+/* The index's current graph as a library-allocated "HNSWGB01" blob (free
+ * with hnsw_free_blob): fp32 vectors (needs F32 storage or the fp32 copy),
+ * levels, both adjacencies and the enter point.  Serialised with inserts. */
+hnsw_status hnsw_index_to_blob(hnsw_index* index, void** out_blob, uint64_t* out_bytes);
+
 typedef struct {
     uint64_t N;
     uint32_t d, d_pad, row_bytes;

@@ -38,9 +38,8 @@
 
 namespace hnswgb {
 // defined in search.cu
-hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const float* q, uint32_t n,
-                          uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
-                          uint32_t* work, const StopModel* stop);
+hnsw_status launch_search_view(hnsw_index* ix, const DevIndex& view, const hnsw_search_params& p, const float* q,
+                               uint32_t n, uint32_t* ids, float* dists, cudaStream_t s, uint32_t* work);
 }  // namespace hnswgb
 
 namespace {
@@ -359,6 +358,115 @@ hnsw_status cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace
 
+namespace hnswgb {
+
+// Inserts the elements `ids` (in order, all of level 0 or already linked on
+// their upper layers) into layer 0 of `view` in batches of at most 1/16 of
+// the elements inserted so far (`inserted` before the first batch), on
+// stream s.  The view's rows must be fp32 (storage F32) and its nbr0 is the
+// adjacency written; asynchronous, buffers freed at return (cudaFree waits
+// for the stream's work).
+hnsw_status insert_layer0(hnsw_index* ix, const DevIndex& view, const std::vector<uint32_t>& ids, uint64_t inserted,
+                          int metric, int M, int Mmax0, int efc, int heuristic, int keep_pruned, cudaStream_t s) {
+    if (ids.empty()) return HNSW_OK;
+    const DevIndex& D = view;
+    const float* drows = reinterpret_cast<const float*>(D.vec);
+    const uint32_t d = D.d, stride = D.row_chunks * 4, dp = D.row_chunks * 4, s0 = D.s0;
+    uint32_t* nbr0 = const_cast<uint32_t*>(D.nbr0);
+    const uint32_t Bmax = uint32_t(std::min<uint64_t>(32768, std::max<uint64_t>(64, ids.size())));
+    DevBuf dbid, dq, rid, rdist, pkey, pval, pdist, skey, sidx, idx, seg, nseg, work, tmp;
+    size_t tmp_bytes = 0;
+    const uint32_t npair_max = Bmax * uint32_t(M);
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, static_cast<uint32_t*>(nullptr),
+                                    static_cast<uint32_t*>(nullptr), static_cast<uint32_t*>(nullptr),
+                                    static_cast<uint32_t*>(nullptr), int(npair_max), 0, 32, s);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](DevBuf& x, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(&x.p, bytes ? bytes : 16);
+    };
+    alloc(dbid, size_t(ids.size()) * 4);
+    alloc(dq, size_t(Bmax) * d * 4);
+    alloc(rid, size_t(Bmax) * efc * 4);
+    alloc(rdist, size_t(Bmax) * efc * 4);
+    alloc(pkey, size_t(npair_max) * 4);
+    alloc(pval, size_t(npair_max) * 4);
+    alloc(pdist, size_t(npair_max) * 4);
+    alloc(skey, size_t(npair_max) * 4);
+    alloc(sidx, size_t(npair_max) * 4);
+    alloc(idx, size_t(npair_max) * 4);
+    alloc(seg, size_t(npair_max) * 4);
+    alloc(nseg, 16);
+    alloc(work, 16);
+    alloc(tmp, tmp_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HNSW_ENOMEM, "layer-0 insertion: device buffers");
+    }
+    std::vector<uint32_t> iota(npair_max);
+    for (uint32_t i = 0; i < npair_max; ++i) iota[i] = i;
+    // pageable sources: the copies complete before cudaMemcpyAsync returns
+    if ((e = cudaMemcpyAsync(idx.p, iota.data(), size_t(npair_max) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dbid.p, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    // warps per block: as many (up to kWarps) as the shared memory allows
+    auto warps_for = [](size_t per_warp) {
+        int nw = kWarps;
+        while (nw > 1 && size_t(nw) * per_warp > 227 * 1024) --nw;
+        return nw;
+    };
+    const int fw_w = warps_for(warp_smem_bytes(M, dp, efc)), rv_w = warps_for(warp_smem_bytes(Mmax0, dp, kKeep));
+    const size_t fw_smem = size_t(fw_w) * warp_smem_bytes(M, dp, efc);
+    const size_t rv_smem = size_t(rv_w) * warp_smem_bytes(Mmax0, dp, kKeep);
+    if (fw_smem > 227 * 1024 || rv_smem > 227 * 1024)
+        return fail(HNSW_EINVAL, "layer-0 insertion: dimension too large for the selection kernels");
+    cudaFuncSetAttribute(select_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fw_smem));
+    cudaFuncSetAttribute(link_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rv_smem));
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    hnsw_search_params sp{};
+    sp.k = efc;
+    sp.ef = efc;
+    hnsw_status st = HNSW_OK;
+    for (size_t pos = 0; pos < ids.size();) {
+        const uint32_t B = uint32_t(std::min<uint64_t>(
+            {uint64_t(Bmax), uint64_t(ids.size() - pos), std::max<uint64_t>(64, inserted / 16)}));
+        const uint32_t* bids = static_cast<const uint32_t*>(dbid.p) + pos;
+        const uint64_t nq = uint64_t(B) * d;
+        gather_rows<<<unsigned((nq + 255) / 256), 256, 0, s>>>(drows, stride, d, bids, B, static_cast<float*>(dq.p));
+        if ((e = cudaMemsetAsync(work.p, 0, 8, s)) != cudaSuccess) break;
+        st = launch_search_view(ix, view, sp, static_cast<const float*>(dq.p), B, static_cast<uint32_t*>(rid.p),
+                                static_cast<float*>(rdist.p), s, static_cast<uint32_t*>(work.p));
+        if (st != HNSW_OK) break;
+        select_forward<<<(B + fw_w - 1) / fw_w, fw_w * 32, fw_smem, s>>>(
+            drows, stride, d, dp, metric, bids, B, static_cast<const uint32_t*>(rid.p),
+            static_cast<const float*>(rdist.p), efc, M, heuristic, keep_pruned, nbr0, s0,
+            static_cast<uint32_t*>(pkey.p), static_cast<uint32_t*>(pval.p), static_cast<float*>(pdist.p));
+        const uint32_t np = B * uint32_t(M);
+        size_t tb = tmp_bytes;
+        if ((e = cub::DeviceRadixSort::SortPairs(tmp.p, tb, static_cast<const uint32_t*>(pkey.p),
+                                                 static_cast<uint32_t*>(skey.p), static_cast<const uint32_t*>(idx.p),
+                                                 static_cast<uint32_t*>(sidx.p), int(np), 0, 32, s)) != cudaSuccess)
+            break;
+        if ((e = cudaMemsetAsync(nseg.p, 0, 4, s)) != cudaSuccess) break;
+        mark_segments<<<(np + 255) / 256, 256, 0, s>>>(static_cast<const uint32_t*>(skey.p), np,
+                                                      static_cast<uint32_t*>(seg.p), static_cast<uint32_t*>(nseg.p));
+        link_reverse<<<unsigned(sms) * 4, rv_w * 32, rv_smem, s>>>(
+            drows, stride, d, dp, metric, static_cast<const uint32_t*>(skey.p), static_cast<const uint32_t*>(sidx.p),
+            np, static_cast<const uint32_t*>(seg.p), static_cast<const uint32_t*>(nseg.p),
+            static_cast<const uint32_t*>(pval.p), static_cast<const float*>(pdist.p), nbr0, s0, Mmax0, heuristic,
+            keep_pruned);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        pos += B;
+        inserted += B;
+    }
+    if (st != HNSW_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "batch");
+    return HNSW_OK;
+}
+
+}  // namespace hnswgb
+
 extern "C" hnsw_status hnsw_build_gpu(const float* data, uint64_t N, uint32_t d, hnsw_metric metric,
                                       const hnsw_build_params* params, const double* level_u, void* stream,
                                       void** out_blob, uint64_t* out_bytes) {
@@ -442,106 +550,15 @@ extern "C" hnsw_status hnsw_build_gpu(const float* data, uint64_t N, uint32_t d,
         hnsw_index* ix;
         ~IxGuard() { hnsw_free_index(ix); }
     } ixg{ix};
-    const DevIndex& D = ix->dev;
-    const float* drows = reinterpret_cast<const float*>(D.vec);
-    const uint32_t stride = D.row_chunks * 4, dp = D.row_chunks * 4, s0 = D.s0;
+    st = insert_layer0(ix, ix->dev, rest, seed.size(), int(metric), int(p.M), int(p.Mmax0),
+                       int(p.ef_construction), p.heuristic, p.keep_pruned, s);
+    if (st != HNSW_OK) {
+        std::free(b);
+        return st;
+    }
     uint32_t* nbr0 = static_cast<uint32_t*>(ix->d_nbr0);
-    const int efc = int(p.ef_construction), M = int(p.M), Mmax0 = int(p.Mmax0);
-    const uint32_t Bmax = uint32_t(std::min<uint64_t>(32768, std::max<uint64_t>(64, rest.size())));
-    DevBuf dbid, dq, rid, rdist, pkey, pval, pdist, skey, sidx, idx, seg, nseg, work, tmp;
-    size_t tmp_bytes = 0;
-    const uint32_t npair_max = Bmax * uint32_t(M);
-    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, static_cast<uint32_t*>(nullptr),
-                                    static_cast<uint32_t*>(nullptr), static_cast<uint32_t*>(nullptr),
-                                    static_cast<uint32_t*>(nullptr), int(npair_max), 0, 32, s);
+    const uint32_t s0 = ix->dev.s0;
     cudaError_t e = cudaSuccess;
-    auto alloc = [&](DevBuf& x, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc(&x.p, bytes ? bytes : 16);
-    };
-    alloc(dbid, size_t(rest.size()) * 4);
-    alloc(dq, size_t(Bmax) * d * 4);
-    alloc(rid, size_t(Bmax) * efc * 4);
-    alloc(rdist, size_t(Bmax) * efc * 4);
-    alloc(pkey, size_t(npair_max) * 4);
-    alloc(pval, size_t(npair_max) * 4);
-    alloc(pdist, size_t(npair_max) * 4);
-    alloc(skey, size_t(npair_max) * 4);
-    alloc(sidx, size_t(npair_max) * 4);
-    alloc(idx, size_t(npair_max) * 4);
-    alloc(seg, size_t(npair_max) * 4);
-    alloc(nseg, 16);
-    alloc(work, 16);
-    alloc(tmp, tmp_bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        std::free(b);
-        return fail(HNSW_ENOMEM, "hnsw_build_gpu: device buffers");
-    }
-    std::vector<uint32_t> iota(npair_max);
-    for (uint32_t i = 0; i < npair_max; ++i) iota[i] = i;
-    if ((e = cudaMemcpyAsync(idx.p, iota.data(), size_t(npair_max) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(dbid.p, rest.data(), rest.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
-        std::free(b);
-        return cuda_fail(e, "copy");
-    }
-    // warps per block: as many (up to kWarps) as the shared memory allows
-    auto warps_for = [](size_t per_warp) {
-        int nw = kWarps;
-        while (nw > 1 && size_t(nw) * per_warp > 227 * 1024) --nw;
-        return nw;
-    };
-    const int fw_w = warps_for(warp_smem_bytes(M, dp, efc)), rv_w = warps_for(warp_smem_bytes(Mmax0, dp, kKeep));
-    const size_t fw_smem = size_t(fw_w) * warp_smem_bytes(M, dp, efc);
-    const size_t rv_smem = size_t(rv_w) * warp_smem_bytes(Mmax0, dp, kKeep);
-    if (fw_smem > 227 * 1024 || rv_smem > 227 * 1024) {
-        std::free(b);
-        return fail(HNSW_EINVAL, "hnsw_build_gpu: dimension too large for the selection kernels");
-    }
-    cudaFuncSetAttribute(select_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fw_smem));
-    cudaFuncSetAttribute(link_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rv_smem));
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    hnsw_search_params sp{};
-    sp.k = efc;
-    sp.ef = efc;
-    uint64_t inserted = seed.size();
-    for (size_t pos = 0; pos < rest.size();) {
-        const uint32_t B = uint32_t(std::min<uint64_t>(
-            {uint64_t(Bmax), uint64_t(rest.size() - pos), std::max<uint64_t>(64, inserted / 16)}));
-        const uint32_t* bids = static_cast<const uint32_t*>(dbid.p) + pos;
-        const uint64_t nq = uint64_t(B) * d;
-        gather_rows<<<unsigned((nq + 255) / 256), 256, 0, s>>>(drows, stride, d, bids, B, static_cast<float*>(dq.p));
-        if ((e = cudaMemsetAsync(work.p, 0, 8, s)) != cudaSuccess) break;
-        st = launch_search(ix, sp, static_cast<const float*>(dq.p), B, static_cast<uint32_t*>(rid.p),
-                           static_cast<float*>(rdist.p), nullptr, s, static_cast<uint32_t*>(work.p), nullptr);
-        if (st != HNSW_OK) break;
-        select_forward<<<(B + fw_w - 1) / fw_w, fw_w * 32, fw_smem, s>>>(
-            drows, stride, d, dp, int(metric), bids, B, static_cast<const uint32_t*>(rid.p),
-            static_cast<const float*>(rdist.p), efc, M, p.heuristic, p.keep_pruned, nbr0, s0,
-            static_cast<uint32_t*>(pkey.p), static_cast<uint32_t*>(pval.p), static_cast<float*>(pdist.p));
-        const uint32_t np = B * uint32_t(M);
-        size_t tb = tmp_bytes;
-        if ((e = cub::DeviceRadixSort::SortPairs(tmp.p, tb, static_cast<const uint32_t*>(pkey.p),
-                                                 static_cast<uint32_t*>(skey.p), static_cast<const uint32_t*>(idx.p),
-                                                 static_cast<uint32_t*>(sidx.p), int(np), 0, 32, s)) != cudaSuccess)
-            break;
-        if ((e = cudaMemsetAsync(nseg.p, 0, 4, s)) != cudaSuccess) break;
-        mark_segments<<<(np + 255) / 256, 256, 0, s>>>(static_cast<const uint32_t*>(skey.p), np,
-                                                      static_cast<uint32_t*>(seg.p), static_cast<uint32_t*>(nseg.p));
-        link_reverse<<<unsigned(sms) * 4, rv_w * 32, rv_smem, s>>>(
-            drows, stride, d, dp, int(metric), static_cast<const uint32_t*>(skey.p),
-            static_cast<const uint32_t*>(sidx.p), np, static_cast<const uint32_t*>(seg.p),
-            static_cast<const uint32_t*>(nseg.p), static_cast<const uint32_t*>(pval.p),
-            static_cast<const float*>(pdist.p), nbr0, s0, Mmax0, p.heuristic, p.keep_pruned);
-        if ((e = cudaGetLastError()) != cudaSuccess) break;
-        pos += B;
-        inserted += B;
-    }
-    if (st != HNSW_OK || e != cudaSuccess) {
-        std::free(b);
-        return st != HNSW_OK ? st : cuda_fail(e, "batch");
-    }
     // 3. the final layer 0 back into the blob
     std::vector<uint32_t> h0(N * size_t(s0));
     if ((e = cudaMemcpyAsync(h0.data(), nbr0, h0.size() * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -552,6 +569,551 @@ extern "C" hnsw_status hnsw_build_gpu(const float* data, uint64_t N, uint32_t d,
     for (uint64_t i = 0; i < N; ++i)
         for (uint32_t c = 0; c < p.Mmax0; ++c) wr<uint32_t>(b + lay.nbr0 + (i * p.Mmax0 + c) * 4, h0[i * s0 + c]);
     finish_header();
+    *out_blob = b;
+    *out_bytes = lay.total;
+    return HNSW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Incremental insertion into a resident index
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ uint64_t mkkey(float d, uint32_t id) { return (uint64_t(f2ord(d)) << 32) | id; }
+__device__ __forceinline__ uint32_t kid(uint64_t k) { return uint32_t(k & 0xffffffffu); }
+__device__ __forceinline__ float kdist(uint64_t k) { return ord2f(uint32_t(k >> 32)); }
+
+// distance from the warp's vector x to row `id` (every lane returns it)
+__device__ __forceinline__ float dist_id(const float (&x)[kMaxDW], const float* rows, uint32_t stride, uint32_t d,
+                                         uint32_t id, int metric, int lane) {
+    float y[kMaxDW];
+    load_vec(rows, stride, d, id, y, lane);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMaxDW; ++k) {
+        if (uint32_t(lane + 32 * k) < d) {
+            if (metric == HNSW_L2SQ) {
+                const float t = x[k] - y[k];
+                s = fmaf(t, t, s);
+            } else {
+                s = fmaf(x[k], y[k], s);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    return metric == HNSW_L2SQ ? s : 1.0f - s;
+}
+
+// min-heap of keys in global memory, touched by lane 0 only
+__device__ void heap_push(uint64_t* h, uint32_t& n, uint64_t k) {
+    uint32_t i = n++;
+    while (i > 0) {
+        const uint32_t p = (i - 1) >> 1;
+        if (h[p] <= k) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i] = k;
+}
+__device__ uint64_t heap_pop(uint64_t* h, uint32_t& n) {
+    const uint64_t top = h[0];
+    const uint64_t last = h[--n];
+    uint32_t i = 0;
+    for (;;) {
+        uint32_t c = 2 * i + 1;
+        if (c >= n) break;
+        if (c + 1 < n && h[c + 1] < h[c]) ++c;
+        if (h[c] >= last) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (n > 0) h[i] = last;
+    return top;
+}
+
+struct UpperArgs {
+    DevIndex v;                 // fp32 view; nbrU / upoff of the version being written
+    const uint32_t* ids;        // new elements of level >= 1, in id order
+    const uint8_t* lv;          // their levels
+    uint32_t n;
+    int efc, M, Mmax, heuristic, keep_pruned;
+    uint32_t* visited;          // [capacity] epoch tags
+    uint64_t* cheap;            // [ccap] candidate min-heap
+    uint32_t ccap;
+    int* state;                 // {enter point, top level}
+};
+
+__device__ __forceinline__ uint32_t* upper_row(const UpperArgs& a, uint32_t e, int lc) {
+    return const_cast<uint32_t*>(a.v.nbrU) + (uint64_t(a.v.upoff[e]) + uint32_t(lc - 1)) * a.v.sU;
+}
+
+// Alg. 1 lines 5-17 on layers >= 1 for each new element in turn (one warp):
+// greedy descent above the element's level, then on each of its layers
+// SEARCH-LAYER with efConstruction, SELECT-NEIGHBORS for its list and the
+// reverse links, shrunk with the same selection beyond Mmax; a new top level
+// makes the element the enter point (lines 18-19).
+__global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    const DevIndex& V = a.v;
+    const float* rows = reinterpret_cast<const float*>(V.vec);
+    const uint32_t d = V.d, stride = V.row_chunks * 4, dp = V.row_chunks * 4;
+    const int ncap = a.efc > kKeep ? a.efc : kKeep;
+    const WarpSmem w = carve(smem, a.Mmax, dp, ncap);
+    uint8_t* p = smem + warp_smem_bytes(a.Mmax, dp, ncap);
+    uint64_t* Wk = reinterpret_cast<uint64_t*>(p);  // [efc + 1] sorted
+    p += size_t(a.efc + 1) * 8;
+    uint64_t* Ek = reinterpret_cast<uint64_t*>(p);  // [efc] enter points of the next layer
+    p += size_t(a.efc) * 8;
+    uint32_t* Wid = reinterpret_cast<uint32_t*>(p);  // [efc] decoded W
+    p += size_t(a.efc) * 4;
+    float* Wd = reinterpret_cast<float*>(p);  // [efc]
+    p += size_t(a.efc) * 4;
+    uint32_t* qR = reinterpret_cast<uint32_t*>(p);  // [64]
+    uint32_t epoch = 0;
+    for (uint32_t u = 0; u < a.n; ++u) {
+        const uint32_t q = a.ids[u];
+        const int l = a.lv[u];
+        __syncwarp();
+        const uint32_t ep = uint32_t(((volatile int*)a.state)[0]);
+        const int L = ((volatile int*)a.state)[1];
+        float xq[kMaxDW];
+        load_vec(rows, stride, d, q, xq, lane);
+        uint32_t cur = ep;
+        float dcur = dist_id(xq, rows, stride, d, ep, V.metric, lane);
+        for (int lc = L; lc > l; --lc) {  // lines 5-7, ef = 1 (steepest descent)
+            for (;;) {
+                const uint32_t* row = upper_row(a, cur, lc);
+                uint32_t best = cur;
+                float db = dcur;
+                for (uint32_t j = 0; j < V.Mmax; ++j) {
+                    const uint32_t e = row[j];
+                    if (e == kNone) break;
+                    const float de = dist_id(xq, rows, stride, d, e, V.metric, lane);
+                    if (mkkey(de, e) < mkkey(db, best)) {
+                        best = e;
+                        db = de;
+                    }
+                }
+                if (best == cur) break;
+                cur = best;
+                dcur = db;
+            }
+        }
+        int n_ep = 1;
+        if (lane == 0) Ek[0] = mkkey(dcur, cur);
+        __syncwarp();
+        for (int lc = l < L ? l : L; lc >= 1; --lc) {
+            // SEARCH-LAYER(q, ep, efc, lc) -- lines 8-9
+            ++epoch;
+            uint32_t wn = 0, cn = 0;
+            if (lane == 0) {
+                for (int i = 0; i < n_ep; ++i) {
+                    const uint64_t k = Ek[i];
+                    a.visited[kid(k)] = epoch;
+                    heap_push(a.cheap, cn, k);
+                    uint32_t j = wn++;
+                    while (j > 0 && Wk[j - 1] > k) {
+                        Wk[j] = Wk[j - 1];
+                        --j;
+                    }
+                    Wk[j] = k;
+                    if (int(wn) > a.efc) wn = uint32_t(a.efc);
+                }
+            }
+            for (;;) {
+                uint64_t c = 0;
+                int go = 0;
+                if (lane == 0 && cn > 0) {
+                    c = heap_pop(a.cheap, cn);
+                    go = c <= Wk[wn - 1];  // key(c) > key(f): stop (line 7)
+                }
+                go = __shfl_sync(kFull, go, 0);
+                if (!go) break;
+                c = __shfl_sync(kFull, c, 0);
+                const uint32_t* row = upper_row(a, kid(c), lc);
+                for (uint32_t j = 0; j < V.Mmax; ++j) {
+                    const uint32_t e = row[j];
+                    if (e == kNone) break;
+                    __syncwarp();
+                    if (a.visited[e] == epoch) continue;
+                    __syncwarp();
+                    if (lane == 0) a.visited[e] = epoch;
+                    const float de = dist_id(xq, rows, stride, d, e, V.metric, lane);
+                    if (lane == 0) {
+                        const uint64_t k = mkkey(de, e);
+                        if (int(wn) < a.efc || k < Wk[wn - 1]) {  // lines 13-17
+                            if (cn < a.ccap) heap_push(a.cheap, cn, k);
+                            uint32_t i = wn < uint32_t(a.efc) ? wn++ : wn - 1;
+                            while (i > 0 && Wk[i - 1] > k) {
+                                Wk[i] = Wk[i - 1];
+                                --i;
+                            }
+                            Wk[i] = k;
+                        }
+                    }
+                }
+            }
+            wn = __shfl_sync(kFull, wn, 0);
+            __syncwarp();
+            for (uint32_t i = lane; i < wn; i += 32) {
+                Wid[i] = kid(Wk[i]);
+                Wd[i] = kdist(Wk[i]);
+                Ek[i] = Wk[i];
+            }
+            n_ep = int(wn);
+            __syncwarp();
+            // neighbourhood(q) at lc -- lines 9-10
+            const int nr = select_links(rows, stride, d, dp, V.metric, Wid, Wd, int(wn), a.M, a.heuristic != 0,
+                                        a.keep_pruned != 0, w, lane);
+            for (int j = lane; j < nr; j += 32) qR[j] = w.Rid[j];
+            __syncwarp();
+            uint32_t* rq = upper_row(a, q, lc);
+            for (uint32_t j = lane; j < V.Mmax; j += 32) rq[j] = int(j) < nr ? qR[j] : kNone;
+            __syncwarp();
+            // reverse links -- lines 11-16
+            for (int t = 0; t < nr; ++t) {
+                const uint32_t r = qR[t];
+                uint32_t* rr = upper_row(a, r, lc);
+                int n0 = 0;
+                for (uint32_t j = lane; j < V.Mmax; j += 32) n0 += rr[j] != kNone;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(kFull, n0, o);
+                if (n0 < int(V.Mmax)) {
+                    if (lane == 0) rr[n0] = q;
+                    __syncwarp();
+                    continue;
+                }
+                float xr[kMaxDW];
+                load_vec(rows, stride, d, r, xr, lane);
+                for (int j = 0; j <= n0; ++j) {
+                    const uint32_t c2 = j < n0 ? rr[j] : q;
+                    const float dc = dist_id(xr, rows, stride, d, c2, V.metric, lane);
+                    if (lane == 0) w.keys[j] = mkkey(dc, c2);
+                }
+                int n2 = 32;
+                while (n2 < n0 + 1) n2 <<= 1;
+                for (int j = n0 + 1 + lane; j < n2; j += 32) w.keys[j] = ~0ull;
+                __syncwarp();
+                sort_keys(w.keys, n2, lane);
+                for (int j = lane; j <= n0; j += 32) {
+                    w.cid[j] = kid(w.keys[j]);
+                    w.cd[j] = kdist(w.keys[j]);
+                }
+                __syncwarp();
+                const int nr2 = select_links(rows, stride, d, dp, V.metric, w.cid, w.cd, n0 + 1, int(V.Mmax),
+                                             a.heuristic != 0, a.keep_pruned != 0, w, lane);
+                for (uint32_t j = lane; j < V.Mmax; j += 32) rr[j] = int(j) < nr2 ? w.Rid[j] : kNone;
+                __syncwarp();
+            }
+        }
+        if (l > L && lane == 0) {  // lines 18-19
+            a.state[0] = int(q);
+            a.state[1] = l;
+        }
+        __threadfence_block();
+        __syncwarp();
+    }
+}
+
+size_t upper_smem_bytes(int Mmax, uint32_t dp, int efc) {
+    const int ncap = efc > kKeep ? efc : kKeep;
+    return warp_smem_bytes(Mmax, dp, ncap) + size_t(efc + 1) * 8 + size_t(efc) * 8 + size_t(efc) * 8 + 64 * 4;
+}
+
+hnsw_status ins_fail(hnsw_status st, const std::string& m) { return fail(st, "hnsw_insert: " + m); }
+
+}  // namespace
+
+extern "C" hnsw_status hnsw_reserve(hnsw_index* ix, uint64_t capacity, void* stream) {
+    if (!ix) return fail(HNSW_EINVAL, "hnsw_reserve: null index");
+    std::lock_guard<std::mutex> lk(ix->insert_mu);
+    const DevIndex D = dev_snapshot(ix);
+    if (capacity < D.N || capacity >= (1ull << 31)) return fail(HNSW_EINVAL, "hnsw_reserve: capacity out of range");
+    if (capacity <= ix->capacity && ix->v_nbr0[1 - ix->active]) return HNSW_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_reserve: ") + cudaGetErrorString(e));
+    const hnsw_index_info& I = ix->info;
+    const uint64_t N = D.N;
+    const uint32_t d_pad32 = D.row_chunks32 * 4;
+    const uint64_t Mm1 = ix->build_M > 1 ? ix->build_M - 1 : 1;
+    const uint64_t ucap = ix->upper_rows + (capacity - N) * 2 / Mm1 + 1024;
+    const bool alias32 = ix->d_vec32 && ix->d_vec32 == ix->d_vec;
+    std::vector<void*> fresh;
+    auto get = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (e == cudaSuccess) e = cudaMalloc(&p, bytes ? bytes : 16);
+        if (e == cudaSuccess) fresh.push_back(p);
+        return p;
+    };
+    void* vec = get(capacity * I.row_bytes);
+    void* scale = ix->d_scale ? get(capacity * 4) : nullptr;
+    void* vec32 = ix->d_vec32 && !alias32 ? get(capacity * d_pad32 * 4ull) : nullptr;
+    void* n0[2] = {get(capacity * D.s0 * 4ull), get(capacity * D.s0 * 4ull)};
+    void* uo[2] = {get(capacity * 4), get(capacity * 4)};
+    void* nu[2] = {get(ucap * D.sU * 4ull), get(ucap * D.sU * 4ull)};
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (void* p : fresh) cudaFree(p);
+        return fail(HNSW_ENOMEM, "hnsw_reserve: device memory");
+    }
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+    };
+    auto ff = [&](void* dst, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemsetAsync(dst, 0xFF, bytes, s);
+    };
+    cp(vec, ix->d_vec, N * I.row_bytes);
+    if (scale) cp(scale, ix->d_scale, N * 4);
+    if (vec32) cp(vec32, ix->d_vec32, N * d_pad32 * 4ull);
+    for (int v = 0; v < 2; ++v) {
+        ff(n0[v], capacity * D.s0 * 4ull);
+        ff(uo[v], capacity * 4);
+        ff(nu[v], ucap * D.sU * 4ull);
+    }
+    cp(n0[0], ix->dev.nbr0, N * D.s0 * 4ull);
+    cp(uo[0], ix->dev.upoff, N * 4);
+    cp(nu[0], ix->dev.nbrU, ix->upper_rows * D.sU * 4ull);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        for (void* p : fresh) cudaFree(p);
+        return fail(HNSW_ECUDA, std::string("hnsw_reserve: copy: ") + cudaGetErrorString(e));
+    }
+    // release the old arrays (both adjacency versions)
+    std::vector<void*> old = {ix->d_vec, ix->d_scale};
+    if (ix->d_vec32 && !alias32) old.push_back(ix->d_vec32);
+    for (int v = 0; v < 2; ++v)
+        for (void* p : {ix->v_nbr0[v], ix->v_upoff[v], ix->v_nbrU[v]}) old.push_back(p);
+    for (void* p : old)
+        if (p) cudaFree(p);
+    ix->d_vec = vec;
+    ix->d_scale = scale;
+    ix->d_vec32 = alias32 ? vec : vec32;
+    for (int v = 0; v < 2; ++v) {
+        ix->v_nbr0[v] = n0[v];
+        ix->v_upoff[v] = uo[v];
+        ix->v_nbrU[v] = nu[v];
+    }
+    ix->active = 0;
+    ix->d_nbr0 = n0[0];
+    ix->d_upoff = uo[0];
+    ix->d_nbrU = nu[0];
+    ix->capacity = capacity;
+    ix->upper_capacity = ucap;
+    {
+        std::lock_guard<std::mutex> dl(ix->dev_mu);
+        ix->dev.vec = static_cast<const uint4*>(vec);
+        ix->dev.scale = static_cast<const float*>(scale);
+        ix->dev.vec32 = static_cast<const uint4*>(ix->d_vec32);
+        ix->dev.nbr0 = static_cast<const uint32_t*>(n0[0]);
+        ix->dev.upoff = static_cast<const uint32_t*>(uo[0]);
+        ix->dev.nbrU = static_cast<const uint32_t*>(nu[0]);
+    }
+    ix->info.device_bytes = capacity * I.row_bytes + (scale ? capacity * 4 : 0) + (vec32 ? capacity * d_pad32 * 4ull : 0) +
+                            2 * (capacity * D.s0 * 4ull + capacity * 4 + ucap * D.sU * 4ull) + kWorkSlots * 4;
+    return HNSW_OK;
+}
+
+extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n, const double* level_u, void* stream) {
+    if (!ix) return ins_fail(HNSW_EINVAL, "null index");
+    if (n == 0) return HNSW_OK;
+    if (!data || !level_u) return ins_fail(HNSW_EINVAL, "null data or level_u");
+    std::lock_guard<std::mutex> lk(ix->insert_mu);
+    DevIndex V = dev_snapshot(ix);
+    const uint64_t N0 = V.N;
+    if (!ix->v_nbr0[1 - ix->active]) return ins_fail(HNSW_EINVAL, "no capacity reserved (hnsw_reserve)");
+    if (N0 + n > ix->capacity) return ins_fail(HNSW_EINVAL, "beyond the reserved capacity");
+    if (V.storage != HNSW_F32 && !V.vec32)
+        return ins_fail(HNSW_EINVAL, "needs the fp32 vectors (F32 storage or keep_fp32_for_rerank)");
+    if (N0 == 0) return ins_fail(HNSW_EINVAL, "the index is empty (build its first elements with hnsw_build)");
+    if (V.d > 32u * kMaxDW) return ins_fail(HNSW_EINVAL, "d above 256");
+    const int efc = int(ix->build_efC), M = int(ix->build_M), Mmax = int(V.Mmax), Mmax0 = int(V.Mmax0);
+    const int heur = (ix->build_flags & 1u) ? 1 : 0, keep = (ix->build_flags & 4u) ? 1 : 0;
+    if ((ix->build_flags & 2u) != 0) return ins_fail(HNSW_EINVAL, "graphs built with extendCandidates");
+    if (efc < 1 || efc > 1024) return ins_fail(HNSW_EINVAL, "efConstruction of the graph outside 1..1024");
+    // levels (Alg. 1 line 4) and the new upper rows, in id order
+    std::vector<uint8_t> lv(n);
+    std::vector<uint32_t> up(n, kNone), U, Z;
+    std::vector<uint8_t> Ul;
+    uint64_t rows = ix->upper_rows;
+    for (uint64_t i = 0; i < n; ++i) {
+        const double u = level_u[i];
+        if (!(u > 0.0 && u <= 1.0)) return ins_fail(HNSW_EINVAL, "level_u outside (0,1]");
+        const double l = std::floor(-std::log(u) * ix->build_mL);
+        if (l > 255) return ins_fail(HNSW_EINVAL, "level above 255");
+        lv[i] = uint8_t(l);
+        if (lv[i] > 0) {
+            up[i] = uint32_t(rows);
+            rows += lv[i];
+            U.push_back(uint32_t(N0 + i));
+            Ul.push_back(lv[i]);
+        } else {
+            Z.push_back(uint32_t(N0 + i));
+        }
+    }
+    if (rows > ix->upper_capacity) return ins_fail(HNSW_EINVAL, "upper-layer rows beyond the reserved capacity");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // searches still reading the version about to be overwritten finish first
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return ins_fail(HNSW_ECUDA, cudaGetErrorString(e));
+    const int act = ix->active, ina = 1 - act;
+    const uint32_t d = V.d, d_pad32 = V.row_chunks32 * 4;
+    DevBuf stage, dU, dUl, visited, cheap, state;
+    auto alloc = [&](DevBuf& x, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(&x.p, bytes ? bytes : 16);
+    };
+    alloc(stage, n * d_pad32 * 4ull);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return ins_fail(HNSW_ENOMEM, "staging");
+    }
+    auto step = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    // the version to write: a copy of the published one, with the new rows empty
+    step(cudaMemcpyAsync(ix->v_nbr0[ina], ix->v_nbr0[act], N0 * V.s0 * 4ull, cudaMemcpyDeviceToDevice, s));
+    step(cudaMemcpyAsync(ix->v_upoff[ina], ix->v_upoff[act], N0 * 4, cudaMemcpyDeviceToDevice, s));
+    step(cudaMemcpyAsync(ix->v_nbrU[ina], ix->v_nbrU[act], ix->upper_rows * V.sU * 4ull, cudaMemcpyDeviceToDevice, s));
+    step(cudaMemsetAsync(static_cast<uint32_t*>(ix->v_nbr0[ina]) + N0 * V.s0, 0xFF, n * V.s0 * 4ull, s));
+    step(cudaMemsetAsync(static_cast<uint32_t*>(ix->v_nbrU[ina]) + ix->upper_rows * V.sU, 0xFF,
+                         (rows - ix->upper_rows) * V.sU * 4ull, s));
+    step(cudaMemcpyAsync(static_cast<uint32_t*>(ix->v_upoff[ina]) + N0, up.data(), n * 4, cudaMemcpyHostToDevice, s));
+    // the vectors: fp32 rows d_pad32 apart, then the stored form
+    step(cudaMemsetAsync(stage.p, 0, n * d_pad32 * 4ull, s));
+    step(cudaMemcpy2DAsync(stage.p, d_pad32 * 4ull, data, d * 4ull, d * 4ull, n, cudaMemcpyDefault, s));
+    if (e != cudaSuccess) return ins_fail(HNSW_ECUDA, std::string("copy: ") + cudaGetErrorString(e));
+    hnsw_status st = store_rows(ix, static_cast<const float*>(stage.p), N0, n, s);
+    if (st != HNSW_OK) return st;
+    // the fp32 view of the version being written
+    V.nbr0 = static_cast<const uint32_t*>(ix->v_nbr0[ina]);
+    V.upoff = static_cast<const uint32_t*>(ix->v_upoff[ina]);
+    V.nbrU = static_cast<const uint32_t*>(ix->v_nbrU[ina]);
+    V.N = uint32_t(N0 + n);
+    if (V.storage != HNSW_F32) {
+        V.vec = V.vec32;
+        V.row_chunks = V.row_chunks32;
+        V.storage = HNSW_F32;
+        V.scale = nullptr;
+    }
+    const int metric = V.metric;
+    // 1. layer 0 of the new elements of level >= 1 (through the old upper layers)
+    st = insert_layer0(ix, V, U, N0, metric, M, Mmax0, efc, heur, keep, s);
+    if (st != HNSW_OK) return st;
+    // 2. their upper layers, one at a time in id order
+    if (!U.empty()) {
+        alloc(dU, U.size() * 4);
+        alloc(dUl, U.size());
+        alloc(visited, (N0 + n) * 4);
+        alloc(cheap, (N0 + n) * 8);
+        alloc(state, 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return ins_fail(HNSW_ENOMEM, "upper-layer buffers");
+        }
+        const int st0[2] = {int(V.ep), V.maxlevel};
+        step(cudaMemcpyAsync(dU.p, U.data(), U.size() * 4, cudaMemcpyHostToDevice, s));
+        step(cudaMemcpyAsync(dUl.p, Ul.data(), U.size(), cudaMemcpyHostToDevice, s));
+        step(cudaMemsetAsync(visited.p, 0, (N0 + n) * 4, s));
+        step(cudaMemcpyAsync(state.p, st0, 8, cudaMemcpyHostToDevice, s));
+        UpperArgs ua{};
+        ua.v = V;
+        ua.ids = static_cast<const uint32_t*>(dU.p);
+        ua.lv = static_cast<const uint8_t*>(dUl.p);
+        ua.n = uint32_t(U.size());
+        ua.efc = efc;
+        ua.M = M;
+        ua.Mmax = Mmax;
+        ua.heuristic = heur;
+        ua.keep_pruned = keep;
+        ua.visited = static_cast<uint32_t*>(visited.p);
+        ua.cheap = static_cast<uint64_t*>(cheap.p);
+        ua.ccap = uint32_t(N0 + n);
+        ua.state = static_cast<int*>(state.p);
+        const size_t sm = upper_smem_bytes(Mmax, V.row_chunks * 4, efc);
+        if (sm > 227 * 1024) return ins_fail(HNSW_EINVAL, "dimension too large for the upper-layer kernel");
+        step(cudaFuncSetAttribute(insert_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+        if (e == cudaSuccess) {
+            insert_upper<<<1, 32, sm, s>>>(ua);
+            e = cudaGetLastError();
+        }
+        int st1[2] = {0, 0};
+        step(cudaMemcpyAsync(st1, state.p, 8, cudaMemcpyDeviceToHost, s));
+        step(cudaStreamSynchronize(s));
+        if (e != cudaSuccess) return ins_fail(HNSW_ECUDA, std::string("upper layers: ") + cudaGetErrorString(e));
+        V.ep = uint32_t(st1[0]);
+        V.maxlevel = st1[1];
+    }
+    // 3. layer 0 of the new elements of level 0
+    st = insert_layer0(ix, V, Z, N0 + U.size(), metric, M, Mmax0, efc, heur, keep, s);
+    if (st != HNSW_OK) return st;
+    step(cudaStreamSynchronize(s));
+    if (e != cudaSuccess) return ins_fail(HNSW_ECUDA, cudaGetErrorString(e));
+    // publish the new version
+    {
+        std::lock_guard<std::mutex> dl(ix->dev_mu);
+        ix->dev.nbr0 = V.nbr0;
+        ix->dev.upoff = V.upoff;
+        ix->dev.nbrU = V.nbrU;
+        ix->dev.N = V.N;
+        ix->dev.ep = V.ep;
+        ix->dev.maxlevel = V.maxlevel;
+    }
+    ix->active = ina;
+    ix->d_nbr0 = ix->v_nbr0[ina];
+    ix->d_upoff = ix->v_upoff[ina];
+    ix->d_nbrU = ix->v_nbrU[ina];
+    ix->upper_rows = rows;
+    ix->levels.insert(ix->levels.end(), lv.begin(), lv.end());
+    ix->info.N = V.N;
+    ix->info.max_level = V.maxlevel;
+    ix->info.enter_point = V.ep;
+    ix->info.n_upper_rows = rows;
+    return HNSW_OK;
+}
+
+extern "C" hnsw_status hnsw_index_to_blob(hnsw_index* ix, void** out_blob, uint64_t* out_bytes) {
+    if (!ix || !out_blob || !out_bytes) return fail(HNSW_EINVAL, "hnsw_index_to_blob: null argument");
+    std::lock_guard<std::mutex> lk(ix->insert_mu);
+    const DevIndex D = dev_snapshot(ix);
+    if (D.storage != HNSW_F32 && !D.vec32)
+        return fail(HNSW_EINVAL, "hnsw_index_to_blob: needs the fp32 vectors (F32 storage or keep_fp32_for_rerank)");
+    const uint64_t N = D.N;
+    const uint32_t d = D.d, d_pad32 = D.row_chunks32 * 4;
+    const BlobLayout lay = BlobLayout::of(N, d, D.Mmax0, D.Mmax, ix->upper_rows);
+    uint8_t* b = static_cast<uint8_t*>(std::calloc(lay.total, 1));
+    if (!b) return fail(HNSW_ENOMEM, "hnsw_index_to_blob: host memory");
+    const void* src32 = D.storage == HNSW_F32 ? static_cast<const void*>(D.vec) : static_cast<const void*>(D.vec32);
+    cudaError_t e = cudaMemcpy2D(b + lay.data, d * 4ull, src32, d_pad32 * 4ull, d * 4ull, N, cudaMemcpyDeviceToHost);
+    std::vector<uint32_t> h0(N * size_t(D.s0)), hu(ix->upper_rows * size_t(D.sU));
+    if (e == cudaSuccess && !h0.empty()) e = cudaMemcpy(h0.data(), D.nbr0, h0.size() * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && !hu.empty()) e = cudaMemcpy(hu.data(), D.nbrU, hu.size() * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        std::free(b);
+        return fail(HNSW_ECUDA, std::string("hnsw_index_to_blob: ") + cudaGetErrorString(e));
+    }
+    std::memcpy(b + lay.level, ix->levels.data(), N);
+    for (uint64_t i = 0; i < N; ++i)
+        for (uint32_t c = 0; c < D.Mmax0; ++c) wr<uint32_t>(b + lay.nbr0 + (i * D.Mmax0 + c) * 4, h0[i * D.s0 + c]);
+    for (uint64_t r = 0; r < ix->upper_rows; ++r)
+        for (uint32_t c = 0; c < D.Mmax; ++c) wr<uint32_t>(b + lay.nbrU + (r * D.Mmax + c) * 4, hu[r * D.sU + c]);
+    BlobHeader h{};
+    h.version = 1;
+    h.metric = uint32_t(D.metric);
+    h.N = N;
+    h.d = d;
+    h.M = ix->build_M;
+    h.Mmax = D.Mmax;
+    h.Mmax0 = D.Mmax0;
+    h.maxlevel = N ? uint32_t(D.maxlevel) : 0;
+    h.ep = N ? D.ep : kNone;
+    h.flags = ix->build_flags;
+    h.efC = ix->build_efC;
+    h.mL = ix->build_mL;
+    h.n_upper_rows = ix->upper_rows;
+    h.checksum = fnv1a64(b + 128, lay.total - 128);
+    write_header(b, h);
     *out_blob = b;
     *out_bytes = lay.total;
     return HNSW_OK;

@@ -203,6 +203,17 @@ extern "C" hnsw_status hnsw_upload_index(const void* graph_blob, uint64_t blob_b
     I.max_level = D.maxlevel;
     I.enter_point = D.ep;
     I.n_upper_rows = h.n_upper_rows;
+    ix->build_M = h.M;
+    ix->build_efC = h.efC;
+    ix->build_flags = h.flags;
+    ix->build_mL = h.mL;
+    ix->levels.assign(b + lay.level, b + lay.level + N);
+    ix->upper_rows = h.n_upper_rows;
+    ix->capacity = N;
+    ix->upper_capacity = h.n_upper_rows;
+    ix->v_nbr0[0] = ix->d_nbr0;
+    ix->v_upoff[0] = ix->d_upoff;
+    ix->v_nbrU[0] = ix->d_nbrU;
     I.device_bytes = N * row_bytes + (ix->d_scale ? N * 4 : 0) + (ix->d_vec32 && storage != HNSW_F32 ? N * d_pad32 * 4ull : 0) +
                      N * s0 * 4ull + N * 4ull + h.n_upper_rows * sU * 4ull + kWorkSlots * 4;
     g.keep = true;
@@ -214,6 +225,10 @@ extern "C" hnsw_status hnsw_free_index(hnsw_index* ix) {
     if (!ix) return HNSW_OK;
     void* ptrs[] = {ix->d_vec, ix->d_scale, ix->d_nbr0, ix->d_upoff, ix->d_nbrU, ix->d_work, ix->d_stop};
     for (void* p : ptrs)
+        if (p) cudaFree(p);
+    // the unpublished adjacency version, when an insertion capacity was reserved
+    const int o = 1 - ix->active;
+    for (void* p : {ix->v_nbr0[o], ix->v_upoff[o], ix->v_nbrU[o]})
         if (p) cudaFree(p);
     for (auto& st : ix->stages)
         if (st.buf) cudaFree(st.buf);
@@ -227,3 +242,29 @@ extern "C" hnsw_status hnsw_get_index_info(const hnsw_index* ix, hnsw_index_info
     *out = ix->info;
     return HNSW_OK;
 }
+
+namespace hnswgb {
+
+hnsw_status store_rows(hnsw_index* ix, const float* rows32, uint64_t first, uint64_t n, cudaStream_t s) {
+    if (n == 0) return HNSW_OK;
+    const hnsw_index_info& I = ix->info;
+    const uint32_t d_pad32 = round_up(I.d, 4);
+    uint8_t* vec = static_cast<uint8_t*>(ix->d_vec) + first * I.row_bytes;
+    cudaError_t e = cudaSuccess;
+    if (I.storage == HNSW_F32) {
+        e = cudaMemcpyAsync(vec, rows32, n * I.row_bytes, cudaMemcpyDeviceToDevice, s);
+    } else {
+        const unsigned blocks = unsigned((n * 32ull + 255) / 256);
+        quantize_rows<<<blocks, 256, 0, s>>>(rows32, d_pad32, n, I.d, I.storage, vec, I.row_bytes,
+                                             ix->d_scale ? static_cast<float*>(ix->d_scale) + first : nullptr);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && ix->d_vec32)
+            e = cudaMemcpyAsync(static_cast<float*>(ix->d_vec32) + first * d_pad32, rows32, n * d_pad32 * 4ull,
+                                cudaMemcpyDeviceToDevice, s);
+    }
+    if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("store rows: ") + cudaGetErrorString(e));
+    return HNSW_OK;
+}
+
+}  // namespace hnswgb
+

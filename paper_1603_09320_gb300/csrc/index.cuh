@@ -86,5 +86,33 @@ struct hnsw_index {
     };
     std::mutex stage_mu;
     std::vector<Stage> stages;
+    // `dev` is read by every launch and replaced by an incremental insertion
+    // when it publishes a new adjacency version: both under dev_mu
+    std::mutex dev_mu;
+    // construction parameters of the graph (from its header) and the levels
+    uint32_t build_M = 0, build_efC = 0, build_flags = 0;
+    double build_mL = 0.0;
+    std::vector<uint8_t> levels;
+    uint64_t upper_rows = 0;  // upper-layer rows in use
+    // incremental insertion (hnsw_reserve / hnsw_insert): rows allocated, and
+    // two versions of the adjacency -- the published one (index `active`) and
+    // the one the next insertion writes
+    uint64_t capacity = 0, upper_capacity = 0;
+    void* v_nbr0[2] = {nullptr, nullptr};
+    void* v_upoff[2] = {nullptr, nullptr};
+    void* v_nbrU[2] = {nullptr, nullptr};
+    int active = 0;
+    std::mutex insert_mu;
     int device = 0;
 };
+
+namespace hnswgb {
+// The index's published device view (a consistent snapshot for one launch).
+inline DevIndex dev_snapshot(hnsw_index* ix) {
+    std::lock_guard<std::mutex> lk(ix->dev_mu);
+    return ix->dev;
+}
+// Writes stored rows [first, first + n) (and the fp32 copy when kept) from
+// fp32 rows in device memory, d_pad32 floats apart; asynchronous on s.
+hnsw_status store_rows(hnsw_index* ix, const float* rows32, uint64_t first, uint64_t n, cudaStream_t s);
+}  // namespace hnswgb

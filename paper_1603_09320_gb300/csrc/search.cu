@@ -1006,8 +1006,8 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
                                uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
                                uint32_t* work, const StopModel* stop, int mode, uint64_t* ep_keys,
                                uint32_t* up_cnt, const uint32_t* order, const uint32_t* q_kef = nullptr,
-                               const uint64_t* q_out = nullptr) {
-    const DevIndex& D = ix->dev;
+                               const uint64_t* q_out = nullptr, const DevIndex* view = nullptr) {
+    const DevIndex D = view ? *view : dev_snapshot(ix);
     KernelChoice kc;
     if (!choose_kernel(D.storage, D.row_chunks, stop != nullptr && stop->period > 0, kc))
         return fail(HNSW_EINVAL, "search: unsupported row size");
@@ -1079,6 +1079,14 @@ hnsw_status launch_search(hnsw_index* ix, const hnsw_search_params& p, const flo
                           uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
                           uint32_t* work, const StopModel* stop) {
     return launch_search_mode(ix, p, q, n, ids, dists, stats, s, work, stop, 0, nullptr, nullptr, nullptr);
+}
+
+// One-pass launch over an explicit device view of the index (graph
+// construction and insertion search views that are not published).
+hnsw_status launch_search_view(hnsw_index* ix, const DevIndex& view, const hnsw_search_params& p, const float* q,
+                               uint32_t n, uint32_t* ids, float* dists, cudaStream_t s, uint32_t* work) {
+    return launch_search_mode(ix, p, q, n, ids, dists, nullptr, s, work, nullptr, 0, nullptr, nullptr, nullptr,
+                              nullptr, nullptr, &view);
 }
 
 // Grouped launch for the server: n queries of several requests on one index,
@@ -1238,11 +1246,13 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     }
     // schedule: 0 automatic (two passes when the batch exceeds the resident
     // warps), 1 one pass in input order, 2 always two passes
+    const DevIndex snap = dev_snapshot(ix);  // both passes search the same version
     const bool two =
-        ix->dev.N > 0 && (p->schedule == 2 || (p->schedule == 0 && uint64_t(n) > 4ull * resident_warps(ix)));
+        snap.N > 0 && (p->schedule == 2 || (p->schedule == 0 && uint64_t(n) > 4ull * resident_warps(ix)));
     hnsw_status r = HNSW_OK;
     if (!two) {
-        r = launch_search(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp);
+        r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 0, nullptr, nullptr, nullptr,
+                               nullptr, nullptr, &snap);
         if (r != HNSW_OK) return r;
     } else {
         // stream-ordered scratch: enter keys [n] u64, upper counters [n][2] u32, order [n] u32
@@ -1256,7 +1266,8 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
         uint64_t* keys = static_cast<uint64_t*>(scr);
         uint32_t* cnt = reinterpret_cast<uint32_t*>(static_cast<char*>(scr) + bk);
         uint32_t* ord = reinterpret_cast<uint32_t*>(static_cast<char*>(scr) + bk + bc);
-        r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 1, keys, cnt, nullptr);
+        r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 1, keys, cnt, nullptr, nullptr,
+                               nullptr, &snap);
         if (r == HNSW_OK) {
             static bool attr = false;
             if (!attr) {
@@ -1269,7 +1280,8 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
             if (e != cudaSuccess) r = fail(HNSW_ECUDA, std::string("hnsw_search: order: ") + cudaGetErrorString(e));
         }
         if (r == HNSW_OK)
-            r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work + 1, smp, 2, keys, cnt, ord);
+            r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work + 1, smp, 2, keys, cnt, ord,
+                                   nullptr, nullptr, &snap);
         cudaFreeAsync(scr, s);
         if (r != HNSW_OK) return r;
     }

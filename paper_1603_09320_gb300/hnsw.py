@@ -93,6 +93,9 @@ def lib():
             "hnsw_build": (i32, [vp, u64, u32, i32, C.POINTER(BuildParams), vp, C.POINTER(vp), C.POINTER(u64)]),
             "hnsw_free_blob": (None, [vp]),
             "hnsw_save_blob": (i32, [vp, u64, C.c_char_p]),
+            "hnsw_reserve": (i32, [vp, u64, vp]),
+            "hnsw_insert": (i32, [vp, vp, u64, vp, vp]),
+            "hnsw_index_to_blob": (i32, [vp, C.POINTER(vp), C.POINTER(u64)]),
             "hnsw_load_blob": (i32, [C.c_char_p, C.POINTER(vp), C.POINTER(u64)]),
             "hnsw_build_gpu": (i32, [vp, u64, u32, i32, C.POINTER(BuildParams), vp, vp, C.POINTER(vp),
                                      C.POINTER(u64)]),
@@ -240,6 +243,39 @@ class Index:
         if getattr(self, "h", None) is not None and self.h.value:
             lib().hnsw_free_index(self.h)
             self.h = None
+
+    def _refresh(self) -> None:
+        _check(lib().hnsw_get_index_info(self.h, C.byref(self.info)))
+
+    def reserve(self, capacity: int, stream=None) -> None:
+        """hnsw_reserve: room for `capacity` elements (incremental insertion)."""
+        _check(lib().hnsw_reserve(self.h, int(capacity), _stream_ptr(stream)))
+        self._refresh()
+
+    def insert(self, data, level_u, stream=None) -> range:
+        """hnsw_insert: appends the rows of `data` (numpy array or CUDA tensor
+        [n][d]) as new elements; returns their ids."""
+        if isinstance(data, np.ndarray):
+            data = np.ascontiguousarray(data, dtype=np.float32)
+        u = np.ascontiguousarray(level_u, dtype=np.float64)
+        n = int(data.shape[0])
+        if u.shape != (n,):
+            raise ValueError("level_u must hold one value per row")
+        first = int(self.info.N)
+        dp, _keep = _ptr(data)
+        _check(lib().hnsw_insert(self.h, dp, n, u.ctypes.data, _stream_ptr(stream)))
+        self._refresh()
+        return range(first, first + n)
+
+    def to_blob(self) -> bytes:
+        """hnsw_index_to_blob: the current graph as an HNSWGB01 blob."""
+        out = C.c_void_p()
+        nbytes = C.c_uint64()
+        _check(lib().hnsw_index_to_blob(self.h, C.byref(out), C.byref(nbytes)))
+        try:
+            return C.string_at(out.value, nbytes.value)
+        finally:
+            lib().hnsw_free_blob(out)
 
     def __del__(self):
         try:
