@@ -102,6 +102,9 @@ def parse():
                     help="selection ablation: Alg. 3 vs Alg. 4 (with and without extendCandidates) on "
                          "clustered low-d data")
     ap.add_argument("--ablation-n", type=int, default=1_000_000)
+    ap.add_argument("--insert", action="store_true",
+                    help="incremental insertion: the last 10% of the bench vectors inserted into a resident index "
+                         "while searches run")
     ap.add_argument("--build-compare", action="store_true",
                     help="graph construction: hnsw_build_gpu against the host builder on the bench workload")
     ap.add_argument("--profile-form", default=None,
@@ -571,6 +574,8 @@ def main():
         return build_compare(args, log)
     if args.ablation:
         return ablation(args, log)
+    if args.insert:
+        return insert_bench(args, log)
 
     import torch
     torch.cuda.set_device(local)
@@ -814,6 +819,86 @@ def ablation(args, log):
         ix.close()
         out["variants"][name] = {"build_s": round(tb, 2), "sweep": rows}
         log(f"ablation {name}: {rows}")
+    print(json.dumps(out), flush=True)
+
+
+def insert_bench(args, log):
+    """Incremental insertion while serving (SIFT-shaped, bf16 + fp32 rerank):
+    the graph of the first 90% of the vectors (host builder) is uploaded, a
+    capacity for all of them reserved, and the last 10% inserted in chunks of
+    10,000 while one host thread keeps searching 10,000-query batches (k=10,
+    ef=52) on its own stream.  Reports insertions/s, the search rate during
+    and without insertion, and recall@10 after insertion beside the graph
+    built by the host builder over all vectors."""
+    import threading
+    import torch
+    from paper_1603_09320_gb300 import build as B
+    from paper_1603_09320_gb300 import graphs, hnsw, synth
+    B.build()
+    X, Q, u = workload(args)
+    N = X.shape[0]
+    n0 = N - N // 10
+    p = synth.params("sift")
+    kw = dict(M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], ef_construction=p["efC"])
+    base = hnsw.build_graph(X[:n0], u[:n0], **kw)
+    full, _ = graph_blob(args, X, u, log)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Qs = Q[:args.n_queries]
+    gt = ground_truth(X, Qs, args.k, dev)
+    q = torch.from_numpy(Qs).to(dev)
+    ix = hnsw.Index(base, "bf16", keep_fp32=True)
+    ix.reserve(N)
+
+    def search_rate(seconds):
+        s = torch.cuda.Stream()
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < seconds:
+            ix.search(q, args.k, 52, rerank=True, stream=s)
+            s.synchronize()
+            n += q.shape[0]
+        return n / (time.perf_counter() - t0)
+
+    idle = search_rate(2.0)
+    done = threading.Event()
+    during = {}
+
+    def reader():
+        torch.cuda.set_device(dev)
+        s = torch.cuda.Stream()
+        n, t0 = 0, time.perf_counter()
+        while not done.is_set():
+            ix.search(q, args.k, 52, rerank=True, stream=s)
+            s.synchronize()
+            n += q.shape[0]
+        during["qps"] = n / (time.perf_counter() - t0)
+
+    th = threading.Thread(target=reader)
+    th.start()
+    ins_stream = torch.cuda.Stream()  # not the legacy default stream: searches keep running beside it
+    t0 = time.perf_counter()
+    for lo in range(n0, N, 10_000):
+        ix.insert(X[lo:min(N, lo + 10_000)], u[lo:min(N, lo + 10_000)], stream=ins_stream)
+    t_ins = time.perf_counter() - t0
+    done.set()
+    th.join()
+    ids, _ = ix.search(q, args.k, 52, rerank=True)
+    torch.cuda.synchronize()
+    r_ins = recall_at(ids.cpu().numpy().view(np.uint32), gt)
+    ix.close()
+    fx = hnsw.Index(full, "bf16", keep_fp32=True)
+    ids, _ = fx.search(q, args.k, 52, rerank=True)
+    torch.cuda.synchronize()
+    r_full = recall_at(ids.cpu().numpy().view(np.uint32), gt)
+    fx.close()
+    out = {"metric": "insertions/s into a resident index while searching, and the search rate",
+           "data": "synthetic", "n_gpus": 1,
+           "config": {"workload": f"SIFT-shaped {N}x{X.shape[1]} (M=16 Mmax0=32 efC=200), bf16 + fp32 rerank; "
+                                  f"{N - n0} elements inserted in chunks of 10,000 into the graph of the first "
+                                  f"{n0}; one host thread searching {Qs.shape[0]}-query batches, k=10, ef=52"},
+           "inserts_per_s": round((N - n0) / t_ins, 1), "insert_seconds": round(t_ins, 3),
+           "search_qps_idle": round(idle, 1), "search_qps_during_insertion": round(during.get("qps", 0.0), 1),
+           "recall_at_10_after_insertion": round(r_ins, 5), "recall_at_10_host_built_full": round(r_full, 5)}
+    log(f"insert: {out}")
     print(json.dumps(out), flush=True)
 
 

@@ -185,7 +185,9 @@ hnsw_status hnsw_reserve(hnsw_index* index, uint64_t capacity, void* stream);
  * a search launched after it sees all of them.  Inserts on one index are
  * serialised.  Needs the fp32 vectors (F32 storage, or keep_fp32_for_rerank)
  * and a non-empty index built by hnsw_build or hnsw_build_gpu without
- * extendCandidates.  Work is issued on `stream`, synchronised before return.
+ * extendCandidates.  Work is issued on `stream`, synchronised before return;
+ * issue it on a stream created non-blocking (not the legacy default stream,
+ * which would serialise the searches of other streams behind the call).
  * Errors: HNSW_EINVAL (null pointers, no reserved capacity, capacity or
  * upper rows exceeded, level_u outside (0,1], d > 256, fp32 vectors absent),
  * HNSW_ENOMEM, HNSW_ECUDA. */

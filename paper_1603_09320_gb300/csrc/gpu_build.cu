@@ -605,6 +605,41 @@ __device__ __forceinline__ float dist_id(const float (&x)[kMaxDW], const float* 
     return metric == HNSW_L2SQ ? s : 1.0f - s;
 }
 
+// distance from the vector a (shared memory, 16-byte aligned, d floats) to
+// row `id`, computed by one lane
+__device__ __forceinline__ float dist_lane(const float* a, const float* rows, uint32_t stride, uint32_t d,
+                                           uint32_t id, int metric) {
+    const float* r = rows + uint64_t(id) * stride;
+    float s = 0.0f;
+    uint32_t c = 0;
+    for (; c + 4 <= d; c += 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(r + c));
+        const float4 q = *reinterpret_cast<const float4*>(a + c);
+        if (metric == HNSW_L2SQ) {
+            const float t0 = q.x - v.x, t1 = q.y - v.y, t2 = q.z - v.z, t3 = q.w - v.w;
+            s = fmaf(t0, t0, s);
+            s = fmaf(t1, t1, s);
+            s = fmaf(t2, t2, s);
+            s = fmaf(t3, t3, s);
+        } else {
+            s = fmaf(q.x, v.x, s);
+            s = fmaf(q.y, v.y, s);
+            s = fmaf(q.z, v.z, s);
+            s = fmaf(q.w, v.w, s);
+        }
+    }
+    for (; c < d; ++c) {
+        const float v = __ldg(r + c);
+        if (metric == HNSW_L2SQ) {
+            const float t = a[c] - v;
+            s = fmaf(t, t, s);
+        } else {
+            s = fmaf(a[c], v, s);
+        }
+    }
+    return metric == HNSW_L2SQ ? s : 1.0f - s;
+}
+
 // min-heap of keys in global memory, touched by lane 0 only
 __device__ void heap_push(uint64_t* h, uint32_t& n, uint64_t k) {
     uint32_t i = n++;
@@ -632,6 +667,50 @@ __device__ uint64_t heap_pop(uint64_t* h, uint32_t& n) {
     return top;
 }
 
+constexpr uint32_t kCcap = 4096;  // candidate heap C of the upper-layer search (shared memory)
+
+// C is full: keep only the candidates not beyond W's furthest element f --
+// a candidate beyond f can never be expanded (the loop stops first), and one
+// not beyond f is still in W, so at most ef remain -- then restore the heap
+__device__ void c_filter(uint64_t* h, uint32_t& n, uint64_t f) {
+    uint32_t m = 0;
+    for (uint32_t i = 0; i < n; ++i)
+        if (h[i] <= f) h[m++] = h[i];
+    n = 0;
+    for (uint32_t i = 0; i < m; ++i) heap_push(h, n, h[i]);
+}
+
+// max-heap of keys in shared memory (the furthest on top), lane 0 only
+__device__ void wheap_push(uint64_t* h, uint32_t& n, uint64_t k) {
+    uint32_t i = n++;
+    while (i > 0) {
+        const uint32_t p = (i - 1) >> 1;
+        if (h[p] >= k) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i] = k;
+}
+__device__ void wheap_replace_top(uint64_t* h, uint32_t n, uint64_t k) {
+    uint32_t i = 0;
+    for (;;) {
+        uint32_t c = 2 * i + 1;
+        if (c >= n) break;
+        if (c + 1 < n && h[c + 1] > h[c]) ++c;
+        if (h[c] <= k) break;
+        h[i] = h[c];
+        i = c;
+    }
+    h[i] = k;
+}
+// W of Alg. 2 capped at ef: k joins when |W| < ef, or replaces the furthest
+__device__ __forceinline__ void w_add(uint64_t* h, uint32_t& n, uint32_t ef, uint64_t k) {
+    if (n < ef)
+        wheap_push(h, n, k);
+    else
+        wheap_replace_top(h, n, k);
+}
+
 struct UpperArgs {
     DevIndex v;                 // fp32 view; nbrU / upoff of the version being written
     const uint32_t* ids;        // new elements of level >= 1, in id order
@@ -639,10 +718,15 @@ struct UpperArgs {
     uint32_t n;
     int efc, M, Mmax, heuristic, keep_pruned;
     uint32_t* visited;          // [capacity] epoch tags
-    uint64_t* cheap;            // [ccap] candidate min-heap
-    uint32_t ccap;
     int* state;                 // {enter point, top level}
 };
+
+// the W buffer: a power of two >= ef (>= 32) for the final bitonic sort
+__host__ __device__ inline int wcap_of(int efc) {
+    int n = 32;
+    while (n < efc) n <<= 1;
+    return n;
+}
 
 __device__ __forceinline__ uint32_t* upper_row(const UpperArgs& a, uint32_t e, int lc) {
     return const_cast<uint32_t*>(a.v.nbrU) + (uint64_t(a.v.upoff[e]) + uint32_t(lc - 1)) * a.v.sU;
@@ -662,8 +746,12 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
     const int ncap = a.efc > kKeep ? a.efc : kKeep;
     const WarpSmem w = carve(smem, a.Mmax, dp, ncap);
     uint8_t* p = smem + warp_smem_bytes(a.Mmax, dp, ncap);
-    uint64_t* Wk = reinterpret_cast<uint64_t*>(p);  // [efc + 1] sorted
-    p += size_t(a.efc + 1) * 8;
+    float* qs = reinterpret_cast<float*>(p);  // [dp] the element being inserted
+    p += size_t(dp) * 4;
+    float* rs = reinterpret_cast<float*>(p);  // [dp] a reverse-link target
+    p += size_t(dp) * 4;
+    uint64_t* Wk = reinterpret_cast<uint64_t*>(p);  // [pow2 >= efc] W: a max-heap, then sorted
+    p += size_t(wcap_of(a.efc)) * 8;
     uint64_t* Ek = reinterpret_cast<uint64_t*>(p);  // [efc] enter points of the next layer
     p += size_t(a.efc) * 8;
     uint32_t* Wid = reinterpret_cast<uint32_t*>(p);  // [efc] decoded W
@@ -671,6 +759,8 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
     float* Wd = reinterpret_cast<float*>(p);  // [efc]
     p += size_t(a.efc) * 4;
     uint32_t* qR = reinterpret_cast<uint32_t*>(p);  // [64]
+    p += 64 * 4;
+    uint64_t* Ch = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));  // [kCcap]
     uint32_t epoch = 0;
     for (uint32_t u = 0; u < a.n; ++u) {
         const uint32_t q = a.ids[u];
@@ -680,25 +770,34 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
         const int L = ((volatile int*)a.state)[1];
         float xq[kMaxDW];
         load_vec(rows, stride, d, q, xq, lane);
+#pragma unroll
+        for (int k = 0; k < kMaxDW; ++k)
+            if (uint32_t(lane + 32 * k) < dp) qs[lane + 32 * k] = xq[k];
+        __syncwarp();
         uint32_t cur = ep;
         float dcur = dist_id(xq, rows, stride, d, ep, V.metric, lane);
         for (int lc = L; lc > l; --lc) {  // lines 5-7, ef = 1 (steepest descent)
             for (;;) {
+                // every neighbour's distance at once (a lane each), then the
+                // smallest key over the warp
                 const uint32_t* row = upper_row(a, cur, lc);
-                uint32_t best = cur;
-                float db = dcur;
-                for (uint32_t j = 0; j < V.Mmax; ++j) {
-                    const uint32_t e = row[j];
-                    if (e == kNone) break;
-                    const float de = dist_id(xq, rows, stride, d, e, V.metric, lane);
-                    if (mkkey(de, e) < mkkey(db, best)) {
-                        best = e;
-                        db = de;
+                uint64_t best = mkkey(dcur, cur);
+                for (uint32_t j0 = 0; j0 < V.Mmax; j0 += 32) {
+                    const uint32_t j = j0 + lane;
+                    const uint32_t e = j < V.Mmax ? row[j] : kNone;
+                    if (e != kNone) {
+                        const uint64_t k = mkkey(dist_lane(qs, rows, stride, d, e, V.metric), e);
+                        best = k < best ? k : best;
                     }
                 }
-                if (best == cur) break;
-                cur = best;
-                dcur = db;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const uint64_t other = __shfl_xor_sync(kFull, best, o);
+                    best = other < best ? other : best;
+                }
+                if (kid(best) == cur) break;
+                cur = kid(best);
+                dcur = kdist(best);
             }
         }
         int n_ep = 1;
@@ -712,51 +811,59 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
                 for (int i = 0; i < n_ep; ++i) {
                     const uint64_t k = Ek[i];
                     a.visited[kid(k)] = epoch;
-                    heap_push(a.cheap, cn, k);
-                    uint32_t j = wn++;
-                    while (j > 0 && Wk[j - 1] > k) {
-                        Wk[j] = Wk[j - 1];
-                        --j;
-                    }
-                    Wk[j] = k;
-                    if (int(wn) > a.efc) wn = uint32_t(a.efc);
+                    heap_push(Ch, cn, k);
+                    if (int(wn) < a.efc || k < Wk[0]) w_add(Wk, wn, uint32_t(a.efc), k);
                 }
             }
             for (;;) {
                 uint64_t c = 0;
                 int go = 0;
                 if (lane == 0 && cn > 0) {
-                    c = heap_pop(a.cheap, cn);
-                    go = c <= Wk[wn - 1];  // key(c) > key(f): stop (line 7)
+                    c = heap_pop(Ch, cn);
+                    go = c <= Wk[0];  // key(c) > key(f): stop (line 7)
                 }
                 go = __shfl_sync(kFull, go, 0);
                 if (!go) break;
                 c = __shfl_sync(kFull, c, 0);
                 const uint32_t* row = upper_row(a, kid(c), lc);
-                for (uint32_t j = 0; j < V.Mmax; ++j) {
-                    const uint32_t e = row[j];
-                    if (e == kNone) break;
-                    __syncwarp();
-                    if (a.visited[e] == epoch) continue;
-                    __syncwarp();
-                    if (lane == 0) a.visited[e] = epoch;
-                    const float de = dist_id(xq, rows, stride, d, e, V.metric, lane);
-                    if (lane == 0) {
-                        const uint64_t k = mkkey(de, e);
-                        if (int(wn) < a.efc || k < Wk[wn - 1]) {  // lines 13-17
-                            if (cn < a.ccap) heap_push(a.cheap, cn, k);
-                            uint32_t i = wn < uint32_t(a.efc) ? wn++ : wn - 1;
-                            while (i > 0 && Wk[i - 1] > k) {
-                                Wk[i] = Wk[i - 1];
-                                --i;
-                            }
-                            Wk[i] = k;
+                // lines 9-11 for every neighbour at once (a lane each; the
+                // list holds distinct ids), then lines 12-17 in list order
+                for (uint32_t j0 = 0; j0 < V.Mmax; j0 += 32) {
+                    const uint32_t j = j0 + lane;
+                    const uint32_t e = j < V.Mmax ? row[j] : kNone;
+                    const bool fresh = e != kNone && a.visited[e] != epoch;
+                    uint64_t k = 0;
+                    if (fresh) {
+                        a.visited[e] = epoch;
+                        k = mkkey(dist_lane(qs, rows, stride, d, e, V.metric), e);
+                    }
+                    // with W full, a neighbour not closer than its furthest element f
+                    // is rejected now and would be by any later f (f only moves
+                    // closer): only the others go through the serial update
+                    const uint32_t wn_now = __shfl_sync(kFull, wn, 0);
+                    const uint64_t f_now = __shfl_sync(kFull, wn_now > 0 ? Wk[0] : ~0ull, 0);
+                    const bool pass = fresh && (int(wn_now) < a.efc || k < f_now);
+                    const unsigned m = __ballot_sync(kFull, pass);
+                    for (unsigned bits = m; bits; bits &= bits - 1) {
+                        const int src = __ffs(bits) - 1;
+                        const uint64_t ke = __shfl_sync(kFull, k, src);
+                        if (lane == 0 && (int(wn) < a.efc || ke < Wk[0])) {  // lines 13-17
+                            if (cn == kCcap) c_filter(Ch, cn, Wk[0]);
+                            heap_push(Ch, cn, ke);
+                            w_add(Wk, wn, uint32_t(a.efc), ke);
                         }
                     }
+                    __syncwarp();
                 }
             }
             wn = __shfl_sync(kFull, wn, 0);
             __syncwarp();
+            {  // W in key order
+                const int n2 = wcap_of(int(wn) > 0 ? int(wn) : 1);
+                for (int i = int(wn) + lane; i < n2; i += 32) Wk[i] = ~0ull;
+                __syncwarp();
+                sort_keys(Wk, n2, lane);
+            }
             for (uint32_t i = lane; i < wn; i += 32) {
                 Wid[i] = kid(Wk[i]);
                 Wd[i] = kdist(Wk[i]);
@@ -787,10 +894,13 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
                 }
                 float xr[kMaxDW];
                 load_vec(rows, stride, d, r, xr, lane);
-                for (int j = 0; j <= n0; ++j) {
+#pragma unroll
+                for (int k = 0; k < kMaxDW; ++k)
+                    if (uint32_t(lane + 32 * k) < dp) rs[lane + 32 * k] = xr[k];
+                __syncwarp();
+                for (int j = lane; j <= n0; j += 32) {  // the members and q, a lane each
                     const uint32_t c2 = j < n0 ? rr[j] : q;
-                    const float dc = dist_id(xr, rows, stride, d, c2, V.metric, lane);
-                    if (lane == 0) w.keys[j] = mkkey(dc, c2);
+                    w.keys[j] = mkkey(dist_lane(rs, rows, stride, d, c2, V.metric), c2);
                 }
                 int n2 = 32;
                 while (n2 < n0 + 1) n2 <<= 1;
@@ -819,7 +929,8 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
 
 size_t upper_smem_bytes(int Mmax, uint32_t dp, int efc) {
     const int ncap = efc > kKeep ? efc : kKeep;
-    return warp_smem_bytes(Mmax, dp, ncap) + size_t(efc + 1) * 8 + size_t(efc) * 8 + size_t(efc) * 8 + 64 * 4;
+    return warp_smem_bytes(Mmax, dp, ncap) + size_t(dp) * 8 + size_t(wcap_of(efc)) * 8 + size_t(efc) * 8 +
+           size_t(efc) * 8 + 64 * 4 + 16 + size_t(kCcap) * 8;
 }
 
 hnsw_status ins_fail(hnsw_status st, const std::string& m) { return fail(st, "hnsw_insert: " + m); }
@@ -960,7 +1071,7 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
     if (e != cudaSuccess) return ins_fail(HNSW_ECUDA, cudaGetErrorString(e));
     const int act = ix->active, ina = 1 - act;
     const uint32_t d = V.d, d_pad32 = V.row_chunks32 * 4;
-    DevBuf stage, dU, dUl, visited, cheap, state;
+    DevBuf stage, dU, dUl, visited, state;
     auto alloc = [&](DevBuf& x, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(&x.p, bytes ? bytes : 16);
     };
@@ -1006,7 +1117,6 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
         alloc(dU, U.size() * 4);
         alloc(dUl, U.size());
         alloc(visited, (N0 + n) * 4);
-        alloc(cheap, (N0 + n) * 8);
         alloc(state, 16);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -1028,8 +1138,6 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
         ua.heuristic = heur;
         ua.keep_pruned = keep;
         ua.visited = static_cast<uint32_t*>(visited.p);
-        ua.cheap = static_cast<uint64_t*>(cheap.p);
-        ua.ccap = uint32_t(N0 + n);
         ua.state = static_cast<int*>(state.p);
         const size_t sm = upper_smem_bytes(Mmax, V.row_chunks * 4, efc);
         if (sm > 227 * 1024) return ins_fail(HNSW_EINVAL, "dimension too large for the upper-layer kernel");

@@ -254,7 +254,9 @@ class Index:
 
     def insert(self, data, level_u, stream=None) -> range:
         """hnsw_insert: appends the rows of `data` (numpy array or CUDA tensor
-        [n][d]) as new elements; returns their ids."""
+        [n][d]) as new elements; returns their ids.  While searches run on
+        other streams, pass a stream of its own (torch.cuda.Stream()): the
+        legacy default stream would serialise them behind the insertion."""
         if isinstance(data, np.ndarray):
             data = np.ascontiguousarray(data, dtype=np.float32)
         u = np.ascontiguousarray(level_u, dtype=np.float64)
