@@ -38,7 +38,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "QPS at recall@10≥0.95, 1M×128, chosen vs plain GPU form; % of HBM-gather roofline"
-EF_SWEEP = [10, 12, 16, 20, 24, 32, 36, 40, 44, 48, 52, 56, 60, 64, 72, 80, 88, 96, 112, 128, 160, 192, 256, 320, 400]
+EF_SWEEP = [10, 12, 16, 20, 24, 32, 36, 40, 44, 48, 50, 52, 54, 56, 60, 64, 72, 80, 88, 96, 112, 128, 160, 192, 256, 320, 400]
 
 
 def max_over_ranks(ms: float, pg) -> float:
