@@ -23,7 +23,7 @@ hnsw_status fail(hnsw_status st, const std::string& msg) {
 }
 
 hnsw_status validate_blob(const uint8_t* b, uint64_t bytes, BlobHeader& h, BlobLayout& lay,
-                          std::vector<uint32_t>& upoff) {
+                          std::vector<uint32_t>& upoff, bool full) {
     if (!b) return fail(HNSW_EINVAL, "blob: null pointer");
     if (!read_header(b, bytes, h)) return fail(HNSW_ECORRUPT, "blob: bad magic, version or size");
     if (h.metric > 1 || h.d == 0 || h.N >= (1ull << 31) || h.Mmax0 == 0 || h.Mmax == 0 || h.Mmax0 > 64 ||
@@ -31,7 +31,7 @@ hnsw_status validate_blob(const uint8_t* b, uint64_t bytes, BlobHeader& h, BlobL
         return fail(HNSW_ECORRUPT, "blob: header fields out of range");
     lay = BlobLayout::of(h.N, h.d, h.Mmax0, h.Mmax, h.n_upper_rows);
     if (lay.total != bytes) return fail(HNSW_ECORRUPT, "blob: size does not match header");
-    if (fnv1a64(b + 128, bytes - 128) != h.checksum) return fail(HNSW_ECORRUPT, "blob: checksum mismatch");
+    if (full && fnv1a64(b + 128, bytes - 128) != h.checksum) return fail(HNSW_ECORRUPT, "blob: checksum mismatch");
     const uint64_t N = h.N;
     const uint8_t* level = b + lay.level;
     if (N > 0) {
@@ -63,6 +63,7 @@ hnsw_status validate_blob(const uint8_t* b, uint64_t bytes, BlobHeader& h, BlobL
         }
         return true;
     };
+    if (!full) return HNSW_OK;
     for (uint64_t i = 0; i < N; ++i) {
         if (!check_row(b + lay.nbr0 + i * h.Mmax0 * 4ull, h.Mmax0, i, 0))
             return fail(HNSW_ECORRUPT, "blob: bad layer-0 list of element " + std::to_string(i));

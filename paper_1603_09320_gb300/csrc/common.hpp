@@ -103,7 +103,9 @@ inline bool read_header(const uint8_t* b, uint64_t bytes, BlobHeader& h) {
 
 // Full structural validation of a blob; on success fills `h`, the layout and
 // the per-element first-upper-row offsets (kNoId for level-0 elements).
+// full = false (a blob the library has just written itself): header, sizes
+// and offsets only -- no checksum, no per-list checks.
 hnsw_status validate_blob(const uint8_t* b, uint64_t bytes, BlobHeader& h, BlobLayout& lay,
-                          std::vector<uint32_t>& upoff);
+                          std::vector<uint32_t>& upoff, bool full = true);
 
 }  // namespace hnswgb

@@ -538,10 +538,12 @@ extern "C" hnsw_status hnsw_build_gpu(const float* data, uint64_t N, uint32_t d,
         h.checksum = fnv1a64(b + 128, lay.total - 128);
         write_header(b, h);
     };
-    finish_header();
-    // 2. layer-0 insertion of the rest on the GPU
+    // 2. layer-0 insertion of the rest on the GPU (the intermediate blob is
+    // uploaded without its checksum or per-list checks: written just above)
+    h.checksum = 0;
+    write_header(b, h);
     hnsw_index* ix = nullptr;
-    st = hnsw_upload_index(b, lay.total, HNSW_F32, 0, stream, &ix);
+    st = upload_index(b, lay.total, HNSW_F32, 0, stream, &ix, true);
     if (st != HNSW_OK) {
         std::free(b);
         return st;

@@ -83,6 +83,15 @@ using namespace hnswgb;
 
 extern "C" hnsw_status hnsw_upload_index(const void* graph_blob, uint64_t blob_bytes, hnsw_dtype storage,
                                          int keep_fp32_for_rerank, void* stream, hnsw_index** out) {
+    return upload_index(graph_blob, blob_bytes, storage, keep_fp32_for_rerank, stream, out, false);
+}
+
+namespace hnswgb {
+
+// hnsw_upload_index; trusted: a blob the library has just written (no
+// checksum or per-list validation)
+hnsw_status upload_index(const void* graph_blob, uint64_t blob_bytes, hnsw_dtype storage, int keep_fp32_for_rerank,
+                         void* stream, hnsw_index** out, bool trusted) {
     if (!out) return fail(HNSW_EINVAL, "hnsw_upload_index: out is null");
     *out = nullptr;
     if (storage < HNSW_F32 || storage > HNSW_F16) return fail(HNSW_EINVAL, "hnsw_upload_index: bad storage");
@@ -90,7 +99,7 @@ extern "C" hnsw_status hnsw_upload_index(const void* graph_blob, uint64_t blob_b
     BlobHeader h{};
     BlobLayout lay{};
     std::vector<uint32_t> upoff;
-    hnsw_status st = validate_blob(b, blob_bytes, h, lay, upoff);
+    hnsw_status st = validate_blob(b, blob_bytes, h, lay, upoff, !trusted);
     if (st != HNSW_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t N = h.N;
@@ -220,6 +229,8 @@ extern "C" hnsw_status hnsw_upload_index(const void* graph_blob, uint64_t blob_b
     *out = holder.release();
     return HNSW_OK;
 }
+
+}  // namespace hnswgb
 
 extern "C" hnsw_status hnsw_free_index(hnsw_index* ix) {
     if (!ix) return HNSW_OK;

@@ -112,6 +112,10 @@ inline DevIndex dev_snapshot(hnsw_index* ix) {
     std::lock_guard<std::mutex> lk(ix->dev_mu);
     return ix->dev;
 }
+// hnsw_upload_index; trusted: skip the checksum and per-list validation of a
+// blob the library has just written itself.
+hnsw_status upload_index(const void* graph_blob, uint64_t blob_bytes, hnsw_dtype storage, int keep_fp32_for_rerank,
+                         void* stream, hnsw_index** out, bool trusted);
 // Writes stored rows [first, first + n) (and the fp32 copy when kept) from
 // fp32 rows in device memory, d_pad32 floats apart; asynchronous on s.
 hnsw_status store_rows(hnsw_index* ix, const float* rows32, uint64_t first, uint64_t n, cudaStream_t s);

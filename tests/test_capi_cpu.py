@@ -114,6 +114,16 @@ def test_graph_file_round_trip_and_rejections(H, oracle, tmp_path):
     assert not (tmp_path / "never.hnsw").exists()
 
 
+def test_insertion_entry_points_reject_null_arguments_without_gpu(H):
+    import ctypes as C
+    L = H.lib()
+    assert L.hnsw_insert(None, None, 1, None, None) != 0
+    assert L.hnsw_reserve(None, 10, None) != 0
+    out, n = C.c_void_p(), C.c_uint64()
+    assert L.hnsw_index_to_blob(None, C.byref(out), C.byref(n)) != 0
+    assert b"null" in H.lib().hnsw_last_error()
+
+
 def test_gpu_builder_rejects_bad_params_without_gpu(H):
     # parameter checks come before any CUDA call
     X = synth.base("tiny", 10)

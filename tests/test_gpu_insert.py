@@ -185,6 +185,33 @@ def test_searches_during_insertion_and_snapshot_equivalence(H, O):
     ix.close()
 
 
+def test_insert_cosine(H, O):
+    # unit-normalised data, cosine distance: a valid graph as good as the
+    # oracle's sequential one over all elements
+    p = dict(synth.params("glove"))
+    p["efC"] = 100
+    N, n0 = 6000, 4000
+    X = synth.base("glove", N)
+    u = synth.level_uniforms("glove", N)
+    base = O.Graph.build(X[:n0], u[:n0], **p)
+    full = O.Graph.build(X, u, **p)
+    ix = H.Index(base.to_blob(), "f32")
+    ix.reserve(N)
+    ix.insert(X[n0:], u[n0:])
+    g = O.Graph.from_blob(ix.to_blob())
+    lv = g.levels()
+    for i in np.nonzero(lv > 0)[0]:  # upper layers: sequential Alg. 1 (fp32 vs fp64 ties aside)
+        assert len(g.neighbors(int(i), 1)) <= p["Mmax"]
+    assert reachable(g) >= reachable(full) - 0.002 * N
+    Q = synth.queries("glove", 300)
+    gt, _ = O.brute_force(X, Q, 10, metric=1)
+    fi = H.Index(full.to_blob(), "f32")
+    for ef in (32, 64):
+        assert recall(search(H, ix, Q, 10, ef)[0], gt) >= recall(search(H, fi, Q, 10, ef)[0], gt) - 0.02
+    fi.close()
+    ix.close()
+
+
 def test_insert_rejections(H, O):
     p, X, u = tiny(3000)
     base = O.Graph.build(X[:2000], u[:2000], **p)
