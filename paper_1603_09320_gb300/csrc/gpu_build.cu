@@ -1024,6 +1024,7 @@ extern "C" hnsw_status hnsw_reserve(hnsw_index* ix, uint64_t capacity, void* str
         ix->dev.upoff = static_cast<const uint32_t*>(uo[0]);
         ix->dev.nbrU = static_cast<const uint32_t*>(nu[0]);
     }
+    std::lock_guard<std::mutex> il(ix->dev_mu);
     ix->info.device_bytes = capacity * I.row_bytes + (scale ? capacity * 4 : 0) + (vec32 ? capacity * d_pad32 * 4ull : 0) +
                             2 * (capacity * D.s0 * 4ull + capacity * 4 + ucap * D.sU * 4ull) + kWorkSlots * 4;
     return HNSW_OK;
@@ -1161,7 +1162,7 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
     step(cudaStreamSynchronize(s));
     if (e != cudaSuccess) return ins_fail(HNSW_ECUDA, cudaGetErrorString(e));
     // publish the new version
-    {
+    {  // the device view and the info together (both read under dev_mu)
         std::lock_guard<std::mutex> dl(ix->dev_mu);
         ix->dev.nbr0 = V.nbr0;
         ix->dev.upoff = V.upoff;
@@ -1169,6 +1170,10 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
         ix->dev.N = V.N;
         ix->dev.ep = V.ep;
         ix->dev.maxlevel = V.maxlevel;
+        ix->info.N = V.N;
+        ix->info.max_level = V.maxlevel;
+        ix->info.enter_point = V.ep;
+        ix->info.n_upper_rows = rows;
     }
     ix->active = ina;
     ix->d_nbr0 = ix->v_nbr0[ina];
@@ -1176,10 +1181,6 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
     ix->d_nbrU = ix->v_nbrU[ina];
     ix->upper_rows = rows;
     ix->levels.insert(ix->levels.end(), lv.begin(), lv.end());
-    ix->info.N = V.N;
-    ix->info.max_level = V.maxlevel;
-    ix->info.enter_point = V.ep;
-    ix->info.n_upper_rows = rows;
     return HNSW_OK;
 }
 

@@ -250,6 +250,8 @@ extern "C" hnsw_status hnsw_free_index(hnsw_index* ix) {
 
 extern "C" hnsw_status hnsw_get_index_info(const hnsw_index* ix, hnsw_index_info* out) {
     if (!ix || !out) return fail(HNSW_EINVAL, "hnsw_get_index_info: null pointer");
+    // an insertion publishes N, top level, enter point and rows under dev_mu
+    std::lock_guard<std::mutex> lk(const_cast<hnsw_index*>(ix)->dev_mu);
     *out = ix->info;
     return HNSW_OK;
 }
