@@ -92,7 +92,7 @@ def parse():
                     default=[0.5, 0.7, 0.8, 0.85, 0.9, 0.95, 0.98])
     ap.add_argument("--stop-period", type=int, default=8)
     ap.add_argument("--stop-epochs", type=int, default=30)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="seconds of oracle search for the CPU baseline")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--serving", action="store_true",
                     help="serving mix: SIFT-shaped 1M and GloVe-shaped 1.2M indexes resident, Poisson requests")
