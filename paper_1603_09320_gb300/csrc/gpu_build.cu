@@ -642,75 +642,21 @@ __device__ __forceinline__ float dist_lane(const float* a, const float* rows, ui
     return metric == HNSW_L2SQ ? s : 1.0f - s;
 }
 
-// min-heap of keys in global memory, touched by lane 0 only
-__device__ void heap_push(uint64_t* h, uint32_t& n, uint64_t k) {
-    uint32_t i = n++;
-    while (i > 0) {
-        const uint32_t p = (i - 1) >> 1;
-        if (h[p] <= k) break;
-        h[i] = h[p];
-        i = p;
-    }
-    h[i] = k;
-}
-__device__ uint64_t heap_pop(uint64_t* h, uint32_t& n) {
-    const uint64_t top = h[0];
-    const uint64_t last = h[--n];
-    uint32_t i = 0;
-    for (;;) {
-        uint32_t c = 2 * i + 1;
-        if (c >= n) break;
-        if (c + 1 < n && h[c + 1] < h[c]) ++c;
-        if (h[c] >= last) break;
-        h[i] = h[c];
-        i = c;
-    }
-    if (n > 0) h[i] = last;
-    return top;
-}
+// keys of the single-list search: (ordered distance, id, expanded bit)
+__device__ __forceinline__ uint64_t lkey(uint64_t k) { return (k & 0xffffffff00000000ull) | (uint64_t(kid(k)) << 1); }
+__device__ __forceinline__ uint32_t lid(uint64_t k) { return uint32_t(k >> 1) & 0x7fffffffu; }
 
-constexpr uint32_t kCcap = 4096;  // candidate heap C of the upper-layer search (shared memory)
-
-// C is full: keep only the candidates not beyond W's furthest element f --
-// a candidate beyond f can never be expanded (the loop stops first), and one
-// not beyond f is still in W, so at most ef remain -- then restore the heap
-__device__ void c_filter(uint64_t* h, uint32_t& n, uint64_t f) {
-    uint32_t m = 0;
-    for (uint32_t i = 0; i < n; ++i)
-        if (h[i] <= f) h[m++] = h[i];
-    n = 0;
-    for (uint32_t i = 0; i < m; ++i) heap_push(h, n, h[i]);
-}
-
-// max-heap of keys in shared memory (the furthest on top), lane 0 only
-__device__ void wheap_push(uint64_t* h, uint32_t& n, uint64_t k) {
-    uint32_t i = n++;
-    while (i > 0) {
-        const uint32_t p = (i - 1) >> 1;
-        if (h[p] >= k) break;
-        h[i] = h[p];
-        i = p;
-    }
-    h[i] = k;
-}
-__device__ void wheap_replace_top(uint64_t* h, uint32_t n, uint64_t k) {
-    uint32_t i = 0;
-    for (;;) {
-        uint32_t c = 2 * i + 1;
-        if (c >= n) break;
-        if (c + 1 < n && h[c + 1] > h[c]) ++c;
-        if (h[c] <= k) break;
-        h[i] = h[c];
-        i = c;
-    }
-    h[i] = k;
-}
-// W of Alg. 2 capped at ef: k joins when |W| < ef, or replaces the furthest
-__device__ __forceinline__ void w_add(uint64_t* h, uint32_t& n, uint32_t ef, uint64_t k) {
-    if (n < ef)
-        wheap_push(h, n, k);
-    else
-        wheap_replace_top(h, n, k);
+// ascending bitonic sort of one key per lane across the warp
+__device__ __forceinline__ uint64_t warp_sort_u64(uint64_t v, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint64_t o = __shfl_xor_sync(kFull, v, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            v = (lower == up) ? (v < o ? v : o) : (v > o ? v : o);
+        }
+    return v;
 }
 
 struct UpperArgs {
@@ -762,7 +708,9 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
     p += size_t(a.efc) * 4;
     uint32_t* qR = reinterpret_cast<uint32_t*>(p);  // [64]
     p += 64 * 4;
-    uint64_t* Ch = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));  // [kCcap]
+    int* LB = reinterpret_cast<int*>(p);  // [32] insertion points of a merge
+    p += 32 * 4;
+    uint64_t* W2 = reinterpret_cast<uint64_t*>(p);  // [pow2 >= efc] merge target
     uint32_t epoch = 0;
     for (uint32_t u = 0; u < a.n; ++u) {
         const uint32_t q = a.ids[u];
@@ -806,70 +754,98 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
         if (lane == 0) Ek[0] = mkkey(dcur, cur);
         __syncwarp();
         for (int lc = l < L ? l : L; lc >= 1; --lc) {
-            // SEARCH-LAYER(q, ep, efc, lc) -- lines 8-9
+            // SEARCH-LAYER(q, ep, efc, lc) -- lines 8-9, in the single-list
+            // form: W sorted by key with an 'expanded' bit below the id; its
+            // unexpanded entries are C (an element that left W can never be
+            // expanded: it lies beyond W's furthest when reached), the next
+            // to expand is the first unexpanded; an expansion's new
+            // neighbours are merged at once (taking them one at a time keeps
+            // W = the ef smallest of W and the ones taken, in any order)
             ++epoch;
-            uint32_t wn = 0, cn = 0;
-            if (lane == 0) {
-                for (int i = 0; i < n_ep; ++i) {
-                    const uint64_t k = Ek[i];
-                    a.visited[kid(k)] = epoch;
-                    heap_push(Ch, cn, k);
-                    if (int(wn) < a.efc || k < Wk[0]) w_add(Wk, wn, uint32_t(a.efc), k);
-                }
+            uint64_t* Wa = Wk;
+            uint64_t* Wb = W2;
+            int wn = n_ep;  // n_ep <= efc (the previous layer's W)
+            for (int i = lane; i < wn; i += 32) {
+                const uint64_t k = Ek[i];
+                a.visited[kid(k)] = epoch;
+                Wa[i] = lkey(k);
             }
+            __syncwarp();
+            int scan = 0;
             for (;;) {
-                uint64_t c = 0;
-                int go = 0;
-                if (lane == 0 && cn > 0) {
-                    c = heap_pop(Ch, cn);
-                    go = c <= Wk[0];  // key(c) > key(f): stop (line 7)
+                int pos = -1;
+                for (int s0 = scan; s0 < wn; s0 += 32) {
+                    const int i = s0 + lane;
+                    const bool un = i < wn && !(Wa[i] & 1ull);
+                    const unsigned m = __ballot_sync(kFull, un);
+                    if (m) {
+                        pos = s0 + __ffs(m) - 1;
+                        break;
+                    }
                 }
-                go = __shfl_sync(kFull, go, 0);
-                if (!go) break;
-                c = __shfl_sync(kFull, c, 0);
-                const uint32_t* row = upper_row(a, kid(c), lc);
-                // lines 9-11 for every neighbour at once (a lane each; the
-                // list holds distinct ids), then lines 12-17 in list order
+                if (pos < 0) break;  // every entry of W expanded (lines 4-8)
+                const uint64_t c = Wa[pos];
+                __syncwarp();
+                if (lane == 0) Wa[pos] = c | 1ull;
+                scan = pos + 1;
+                const uint32_t* row = upper_row(a, lid(c), lc);
                 for (uint32_t j0 = 0; j0 < V.Mmax; j0 += 32) {
+                    // lines 9-12 for every neighbour at once, a lane each
                     const uint32_t j = j0 + lane;
                     const uint32_t e = j < V.Mmax ? row[j] : kNone;
                     const bool fresh = e != kNone && a.visited[e] != epoch;
-                    uint64_t k = 0;
+                    uint64_t k = ~0ull;
                     if (fresh) {
                         a.visited[e] = epoch;
-                        k = mkkey(dist_lane(qs, rows, stride, d, e, V.metric), e);
+                        k = (uint64_t(f2ord(dist_lane(qs, rows, stride, d, e, V.metric))) << 32) | (uint64_t(e) << 1);
                     }
-                    // with W full, a neighbour not closer than its furthest element f
-                    // is rejected now and would be by any later f (f only moves
-                    // closer): only the others go through the serial update
-                    const uint32_t wn_now = __shfl_sync(kFull, wn, 0);
-                    const uint64_t f_now = __shfl_sync(kFull, wn_now > 0 ? Wk[0] : ~0ull, 0);
-                    const bool pass = fresh && (int(wn_now) < a.efc || k < f_now);
+                    // lines 13-17: with W full only keys below its furthest enter
+                    const bool pass = fresh && (wn < a.efc || k < (Wa[wn - 1] & ~1ull));
                     const unsigned m = __ballot_sync(kFull, pass);
-                    for (unsigned bits = m; bits; bits &= bits - 1) {
-                        const int src = __ffs(bits) - 1;
-                        const uint64_t ke = __shfl_sync(kFull, k, src);
-                        if (lane == 0 && (int(wn) < a.efc || ke < Wk[0])) {  // lines 13-17
-                            if (cn == kCcap) c_filter(Ch, cn, Wk[0]);
-                            heap_push(Ch, cn, ke);
-                            w_add(Wk, wn, uint32_t(a.efc), ke);
+                    if (!m) continue;
+                    const int nb = __popc(m);
+                    const uint64_t key = warp_sort_u64(pass ? k : ~0ull, lane);  // lane j: j-th smallest
+                    int lb = 0;
+                    if (lane < nb) {  // old entries below the key
+                        int lo = 0, hi = wn;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if ((Wa[mid] & ~1ull) < key)
+                                lo = mid + 1;
+                            else
+                                hi = mid;
                         }
+                        lb = lo;
+                        LB[lane] = lb;
                     }
+                    __syncwarp();
+                    const int nn = wn + nb < a.efc ? wn + nb : a.efc;
+                    for (int i = lane; i < wn; i += 32) {  // old entry i moves up by the new keys below it
+                        int lo = 0, hi = nb;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (LB[mid] <= i)
+                                lo = mid + 1;
+                            else
+                                hi = mid;
+                        }
+                        if (i + lo < nn) Wb[i + lo] = Wa[i];
+                    }
+                    if (lane < nb && lb + lane < nn) Wb[lb + lane] = key;
+                    __syncwarp();
+                    if (LB[0] < scan) scan = LB[0];  // the smallest new key may precede the scan
+                    uint64_t* t = Wa;
+                    Wa = Wb;
+                    Wb = t;
+                    wn = nn;
                     __syncwarp();
                 }
             }
-            wn = __shfl_sync(kFull, wn, 0);
-            __syncwarp();
-            {  // W in key order
-                const int n2 = wcap_of(int(wn) > 0 ? int(wn) : 1);
-                for (int i = int(wn) + lane; i < n2; i += 32) Wk[i] = ~0ull;
-                __syncwarp();
-                sort_keys(Wk, n2, lane);
-            }
-            for (uint32_t i = lane; i < wn; i += 32) {
-                Wid[i] = kid(Wk[i]);
-                Wd[i] = kdist(Wk[i]);
-                Ek[i] = Wk[i];
+            for (int i = lane; i < wn; i += 32) {
+                const uint64_t k = Wa[i];
+                Wid[i] = lid(k);
+                Wd[i] = kdist(k);
+                Ek[i] = (k & 0xffffffff00000000ull) | lid(k);
             }
             n_ep = int(wn);
             __syncwarp();
@@ -932,7 +908,7 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
 size_t upper_smem_bytes(int Mmax, uint32_t dp, int efc) {
     const int ncap = efc > kKeep ? efc : kKeep;
     return warp_smem_bytes(Mmax, dp, ncap) + size_t(dp) * 8 + size_t(wcap_of(efc)) * 8 + size_t(efc) * 8 +
-           size_t(efc) * 8 + 64 * 4 + 16 + size_t(kCcap) * 8;
+           size_t(efc) * 8 + 64 * 4 + 32 * 4 + size_t(wcap_of(efc)) * 8;
 }
 
 hnsw_status ins_fail(hnsw_status st, const std::string& m) { return fail(st, "hnsw_insert: " + m); }
