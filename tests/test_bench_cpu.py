@@ -1,0 +1,60 @@
+"""Host-side helpers of bench.py: recall, tie-tolerant recall, the host exact
+k-NN and the threaded oracle runner (no GPU)."""
+import os
+import sys
+
+import numpy as np
+
+from paper_1603_09320_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def set_recall(ids, gt):
+    return sum(len(set(ids[i].tolist()) & set(gt[i].tolist())) for i in range(len(gt))) / gt.size
+
+
+def test_recall_matches_the_set_definition():
+    rng = np.random.default_rng(3)
+    gt = np.array([rng.choice(1000, 10, replace=False) for _ in range(200)])
+    ids = np.array([rng.choice(1000, 10, replace=False) for _ in range(200)])
+    ids[:50] = gt[:50][:, ::-1]  # some exact rows, in another order
+    assert bench.recall_at(ids, gt) == set_recall(ids, gt)
+    assert bench.recall_at(gt, gt) == 1.0
+
+
+def test_tie_tolerant_recall_counts_ties_at_the_kth_distance():
+    rng = np.random.default_rng(0)
+    X = rng.integers(0, 4, (500, 4)).astype(np.float32)  # many equal distances
+    Q = rng.integers(0, 4, (50, 4)).astype(np.float32)
+    gt = bench.exact_knn_numpy(X, Q, 5)
+    alt = np.array([np.lexsort((-np.arange(500), ((X - Q[i]) ** 2).sum(1)))[:5] for i in range(50)])
+    assert bench.recall_at(alt, gt) < 1.0  # ties broken the other way
+    assert bench.recall_tie_tolerant(X, Q, alt, gt) == 1.0
+    far = np.tile(np.argsort(-((X - Q[0]) ** 2).sum(1))[:5], (50, 1))
+    assert bench.recall_tie_tolerant(X, Q, far, gt) <= bench.recall_at(far, gt) + 0.2
+
+
+def test_host_exact_knn_equals_the_oracle_brute_force():
+    from oracle import oracle as O
+    X = synth.base("tiny", 3000)
+    Q = synth.queries("tiny", 40)
+    ids, _ = O.brute_force(X, Q, 10)
+    np.testing.assert_array_equal(bench.exact_knn_numpy(X, Q, 10), ids.astype(np.int64))
+
+
+def test_threaded_oracle_runner_matches_one_thread():
+    from oracle import oracle as O
+    p = synth.params("tiny")
+    X = synth.base("tiny", 2000)
+    g = O.Graph.build(X, synth.level_uniforms("tiny", 2000), **p)
+    Q = synth.queries("tiny", 64)
+    one, _, _ = bench.oracle_run(g, Q, 10, 32, 1, 1e9)
+    many, bounds, _ = bench.oracle_run(g, Q, 10, 32, 4, 1e9)
+    a = np.array([i for part in one for i in part[0]])
+    b = np.array([i for part in many for i in part[0]])
+    np.testing.assert_array_equal(a, b)
+    assert list(bounds) == [0, 16, 32, 48, 64]
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
