@@ -102,6 +102,8 @@ def parse():
                     help="selection ablation: Alg. 3 vs Alg. 4 (with and without extendCandidates) on "
                          "clustered low-d data")
     ap.add_argument("--ablation-n", type=int, default=1_000_000)
+    ap.add_argument("--angular", action="store_true",
+                    help="GloVe-shaped 1.2M cosine: fixed-ef sweep against the learned stop (bf16 + fp32 rerank)")
     ap.add_argument("--insert", action="store_true",
                     help="incremental insertion: the last 10% of the bench vectors inserted into a resident index "
                          "while searches run")
@@ -275,7 +277,7 @@ def run_forms(args, blob, X, Q, gt, log):
     return res, indexes, bufs
 
 
-def stop_form(args, ix, X, bufs, gt, rerank, log):
+def stop_form(args, ix, X, bufs, gt, rerank, log, workload="sift", metric=0):
     """Learned early stop on top of the given index: traces of separate
     training queries at ef_max, labels against their exact k-NN, training on
     the GPU, then the (ef_max, threshold) pair with the best time among those
@@ -283,8 +285,8 @@ def stop_form(args, ix, X, bufs, gt, rerank, log):
     import torch
     from paper_1603_09320_gb300 import stopnet, synth
     k = args.k
-    Qt = synth.queries("sift", args.train_queries, training=True)
-    gt_t = ground_truth(X, Qt, k, bufs[0].device)
+    Qt = synth.queries(workload, args.train_queries, training=True)
+    gt_t = ground_truth(X, Qt, k, bufs[0].device) if metric == 0 else ground_truth_metric(X, Qt, k, metric)
     qt = torch.from_numpy(Qt).cuda()
     info = {"train_queries": int(Qt.shape[0]), "models": {}}
     sweep = []
@@ -576,6 +578,8 @@ def main():
         return ablation(args, log)
     if args.insert:
         return insert_bench(args, log)
+    if args.angular:
+        return angular_bench(args, log)
 
     import torch
     torch.cuda.set_device(local)
@@ -819,6 +823,85 @@ def ablation(args, log):
         ix.close()
         out["variants"][name] = {"build_s": round(tb, 2), "sweep": rows}
         log(f"ablation {name}: {rows}")
+    print(json.dumps(out), flush=True)
+
+
+def angular_bench(args, log):
+    """Angular workload with learned early termination: GloVe-shaped 1.2M x
+    100 unit vectors, cosine, M=16, efConstruction=500 (graph built by
+    hnsw_build_gpu), bf16 storage + fp32 rerank, 10,000 queries, k=10.  The
+    fixed-ef sweep (refined between its last two points) gives the smallest
+    ef reaching recall@10 >= 0.95; the
+    learned stop is trained on traces of args.train_queries training queries
+    at ef_max = 1x, 1.5x and 2x that ef and swept over thresholds; every
+    setting is timed as the main bench's region (consecutive batches on two
+    streams)."""
+    import torch
+    from paper_1603_09320_gb300 import build as B
+    from paper_1603_09320_gb300 import hnsw, synth
+    B.build()
+    name = "glove"
+    p = synth.params(name)
+    X = synth.base(name)
+    u = synth.level_uniforms(name)
+    t0 = time.perf_counter()
+    blob = hnsw.build_graph_gpu(X, u, metric=p["metric"], M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"],
+                                ef_construction=p["efC"])
+    t_build = time.perf_counter() - t0
+    log(f"angular: graph built on the GPU in {t_build:.1f}s")
+    Q = synth.queries(name, args.n_queries)
+    gt = ground_truth_metric(X, Q, args.k, p["metric"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    q = torch.from_numpy(Q).to(dev)
+    n, k = Q.shape[0], args.k
+    bufs = (q, torch.empty((n, k), dtype=torch.int32, device=dev), torch.empty((n, k), dtype=torch.float32, device=dev),
+            torch.empty((n, 4), dtype=torch.int32, device=dev))
+    ix = hnsw.Index(blob, "bf16", keep_fp32=True)
+    sweep, ef_ok = [], None
+
+    def recall_of(ef):
+        _search(ix, args, bufs, {"ef": ef, "rerank": True})
+        torch.cuda.synchronize()
+        r = recall_at(bufs[1].cpu().numpy().view(np.uint32), gt)
+        sweep.append((ef, round(r, 5)))
+        return r
+
+    grid = [10, 16, 24, 32, 40, 48, 56, 64, 80, 96, 112, 128, 160, 192, 256, 320, 400, 512, 640, 800]
+    lo = 0
+    for ef in grid:
+        r = recall_of(ef)
+        if r >= args.target_recall:
+            ef_ok = {"ef": ef, "rerank": True, "recall": r}
+            break
+        lo = ef
+    if ef_ok is not None and lo > 0:  # the smallest ef on a finer grid between the last two points
+        step = max(4, (ef_ok["ef"] - lo) // 8)
+        for ef in range(lo + step, ef_ok["ef"], step):
+            r = recall_of(ef)
+            if r >= args.target_recall:
+                ef_ok = {"ef": ef, "rerank": True, "recall": r}
+                break
+    log(f"angular: fixed-ef sweep {sweep}")
+    if ef_ok is None:
+        raise SystemExit("fixed ef never reached the target recall")
+    ms_fixed, _ = time_pipelined(args, ix, ef_ok, q, 20, 3)
+    ef0 = ef_ok["ef"]
+    args.stop_efs = sorted({ef0, int(ef0 * 1.5), 2 * ef0})
+    st = stop_form(args, ix, X, bufs, gt, True, log, workload=name, metric=p["metric"])
+    ms_stop = None
+    if st["setting"] is not None:
+        ms_stop, _ = time_pipelined(args, ix, st["setting"], q, 20, 3)
+    ix.close()
+    out = {"metric": "queries/s at recall@10 >= 0.95: learned stop vs fixed ef (bf16 + fp32 rerank)",
+           "data": "synthetic", "n_gpus": 1,
+           "config": {"workload": f"GloVe-shaped {X.shape[0]}x{X.shape[1]} unit vectors, cosine, M=16 efC=500, "
+                                  f"{n} queries, k=10; stop network trained on {args.train_queries} training queries",
+                      "graph_build_gpu_s": round(t_build, 2)},
+           "fixed_ef": {"setting": ef_ok, "sweep": sweep, "ms_per_step": round(ms_fixed, 4),
+                        "qps": round(n / (ms_fixed / 1e3), 1)},
+           "learned_stop": {"setting": st["setting"], "sweep": st["sweep"], "training": st["training"],
+                            "ms_per_step": round(ms_stop, 4) if ms_stop else None,
+                            "qps": round(n / (ms_stop / 1e3), 1) if ms_stop else None}}
     print(json.dumps(out), flush=True)
 
 
