@@ -4,17 +4,19 @@
  * Hierarchical Navigable Small World graphs (Malkov & Yashunin,
  * arXiv:1603.09320).  The library builds the multilayer graph on the host
  * (Alg. 1 INSERT with Alg. 4 SELECT-NEIGHBORS-HEURISTIC, multi-threaded as in
- * Section 4.1) and answers batches of K-NN queries on one GPU (Alg. 5
- * K-NN-SEARCH: greedy ef=1 descent through layers L..1 followed by the
- * ef-bounded SEARCH-LAYER of Alg. 2 on layer 0), in hand-written sm_103a
- * CUDA kernels.
+ * Section 4.1) or with its layer-0 insertions on the GPU, answers batches of
+ * K-NN queries on one GPU (Alg. 5 K-NN-SEARCH: greedy ef=1 descent through
+ * layers L..1 followed by the ef-bounded SEARCH-LAYER of Alg. 2 on layer 0),
+ * and inserts new elements into a resident index while it serves searches,
+ * in hand-written sm_103a CUDA kernels.
  *
  * Conventions for every entry point:
  *  - Return an hnsw_status; no C++ exception crosses the ABI.  On failure,
  *    hnsw_last_error() gives a message for the calling thread.
  *  - The caller owns query and output buffers; the library owns the memory of
- *    an index (device memory allocated by hnsw_upload_index, freed by
- *    hnsw_free_index) and of blobs it returns (freed by hnsw_free_blob).
+ *    an index (device memory allocated by hnsw_upload_index and
+ *    hnsw_reserve, freed by hnsw_free_index) and of blobs it returns (freed
+ *    by hnsw_free_blob).
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).
  *  - Element ids are uint32; 0xFFFFFFFF (HNSW_NO_ID) marks "no element".
  *  - Distances are squared L2, or cosine distance 1 - <q,x> on unit vectors
