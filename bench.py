@@ -104,6 +104,9 @@ def parse():
     ap.add_argument("--ablation-n", type=int, default=1_000_000)
     ap.add_argument("--angular", action="store_true",
                     help="GloVe-shaped 1.2M cosine: fixed-ef sweep against the learned stop (bf16 + fp32 rerank)")
+    ap.add_argument("--lowd", action="store_true",
+                    help="low-d clustered 10M x 8: plain fp32 vs fp16 + rerank vs learned stop")
+    ap.add_argument("--lowd-n", type=int, default=10_000_000)
     ap.add_argument("--insert", action="store_true",
                     help="incremental insertion: the last 10% of the bench vectors inserted into a resident index "
                          "while searches run")
@@ -286,7 +289,10 @@ def stop_form(args, ix, X, bufs, gt, rerank, log, workload="sift", metric=0):
     from paper_1603_09320_gb300 import stopnet, synth
     k = args.k
     Qt = synth.queries(workload, args.train_queries, training=True)
-    gt_t = ground_truth(X, Qt, k, bufs[0].device) if metric == 0 else ground_truth_metric(X, Qt, k, metric)
+    if workload == "lowd":  # tight clusters: the fp32 expansion cancels
+        gt_t = exact_knn_fp64(X, Qt, k, bufs[0].device)
+    else:
+        gt_t = ground_truth(X, Qt, k, bufs[0].device) if metric == 0 else ground_truth_metric(X, Qt, k, metric)
     qt = torch.from_numpy(Qt).cuda()
     info = {"train_queries": int(Qt.shape[0]), "models": {}}
     sweep = []
@@ -583,6 +589,8 @@ def main():
         return insert_bench(args, log)
     if args.angular:
         return angular_bench(args, log)
+    if args.lowd:
+        return lowd_bench(args, log)
 
     import torch
     torch.cuda.set_device(local)
@@ -905,6 +913,90 @@ def angular_bench(args, log):
            "learned_stop": {"setting": st["setting"], "sweep": st["sweep"], "training": st["training"],
                             "ms_per_step": round(ms_stop, 4) if ms_stop else None,
                             "qps": round(n / (ms_stop / 1e3), 1) if ms_stop else None}}
+    print(json.dumps(out), flush=True)
+
+
+def exact_knn_fp64(X, Q, k, device):
+    """Exact k-NN on the GPU in fp64 (|x|^2 - 2 x.q + |q|^2 keeps ~1e-16
+    relative error, far below the 1e-6 squared spread of sigma 1e-3
+    clusters): a shortlist of 32 per query, rescored in fp64 on the host by
+    key (distance, id)."""
+    import torch
+    Xd = torch.from_numpy(X).to(device, torch.float64)
+    xn = (Xd * Xd).sum(1)
+    out = np.zeros((Q.shape[0], k), dtype=np.int64)
+    for s0 in range(0, Q.shape[0], 64):
+        q = torch.from_numpy(Q[s0:s0 + 64]).to(device, torch.float64)
+        d = xn[None, :] - 2.0 * (q @ Xd.T)
+        cand = torch.topk(d, 32, dim=1, largest=False).indices.cpu().numpy()
+        for i in range(cand.shape[0]):
+            c = cand[i]
+            ex = ((X[c].astype(np.float64) - Q[s0 + i].astype(np.float64)) ** 2).sum(1)
+            out[s0 + i] = c[np.lexsort((c, ex))[:k]]
+    del Xd
+    torch.cuda.empty_cache()
+    return out
+
+
+def lowd_bench(args, log):
+    """Low-dimensional clustered data: args.lowd_n x 8 (95% in 10,000
+    clusters of sigma 1e-3, 5% uniform), squared L2, M=12, Mmax0=24, efC=100,
+    graph by hnsw_build_gpu; 10,000 queries (90% cluster-drawn), k=10 (and
+    recall@1 of the first result).  Plain fp32 and fp16 + fp32 rerank at the
+    smallest ef reaching recall@10 >= 0.95, and the learned stop on fp32
+    (trained on traces of args.train_queries training queries); every
+    setting timed as the main bench's region."""
+    import torch
+    from paper_1603_09320_gb300 import build as B
+    from paper_1603_09320_gb300 import hnsw, synth
+    B.build()
+    name, N = "lowd", args.lowd_n
+    p = synth.params(name)
+    X = synth.base(name, N)
+    u = synth.level_uniforms(name, N)
+    t0 = time.perf_counter()
+    blob = hnsw.build_graph_gpu(X, u, M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], ef_construction=p["efC"])
+    t_build = time.perf_counter() - t0
+    log(f"lowd: graph of {N} built on the GPU in {t_build:.1f}s")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Q = synth.queries(name, args.n_queries)
+    gt = exact_knn_fp64(X, Q, args.k, dev)
+    log("lowd: ground truth done")
+    q = torch.from_numpy(Q).to(dev)
+    n, k = Q.shape[0], args.k
+    bufs = (q, torch.empty((n, k), dtype=torch.int32, device=dev), torch.empty((n, k), dtype=torch.float32, device=dev),
+            torch.empty((n, 4), dtype=torch.int32, device=dev))
+    out = {"metric": "queries/s at recall@10 >= 0.95 on clustered low-d data", "data": "synthetic", "n_gpus": 1,
+           "config": {"workload": f"low-d clustered {N}x8 (95% in 10,000 clusters, sigma 1e-3; 5% uniform), "
+                                  f"M=12 Mmax0=24 efC=100, {n} queries (90% cluster-drawn), k=10",
+                      "graph_build_gpu_s": round(t_build, 2)}, "forms": {}}
+    for form, storage, rr in (("f32", "f32", False), ("f16r", "f16", True)):
+        ix = hnsw.Index(blob, storage, keep_fp32=rr)
+        sweep, ok = [], None
+        for ef in [10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 200, 256, 320, 400]:
+            cand = {"ef": ef, "rerank": rr}
+            _search(ix, args, bufs, cand)
+            torch.cuda.synchronize()
+            ids = bufs[1].cpu().numpy().view(np.uint32)
+            r = recall_at(ids, gt)
+            r1 = float((ids[:, 0].astype(np.int64) == gt[:, 0]).mean())
+            sweep.append((ef, round(r, 5), round(r1, 5)))
+            if r >= args.target_recall:
+                ok = dict(cand, recall=r, recall_at_1=r1)
+                break
+        ms = time_pipelined(args, ix, ok, q, 20, 3)[0] if ok else None
+        out["forms"][form] = {"setting": ok, "sweep": sweep, "ms_per_step": round(ms, 4) if ms else None,
+                              "qps": round(n / (ms / 1e3), 1) if ms else None}
+        log(f"lowd: {form} {out['forms'][form]}")
+        if form == "f32" and ok:
+            args.stop_efs = sorted({ok["ef"], int(ok["ef"] * 1.5), 2 * ok["ef"]})
+            st = stop_form(args, ix, X, bufs, gt, False, log, workload=name, metric=0)
+            ms_s = time_pipelined(args, ix, st["setting"], q, 20, 3)[0] if st["setting"] else None
+            out["forms"]["f32_stop"] = {"setting": st["setting"], "sweep": st["sweep"],
+                                        "ms_per_step": round(ms_s, 4) if ms_s else None,
+                                        "qps": round(n / (ms_s / 1e3), 1) if ms_s else None}
+            log(f"lowd: f32_stop {out['forms']['f32_stop']['setting']} {out['forms']['f32_stop']['ms_per_step']}")
+        ix.close()
     print(json.dumps(out), flush=True)
 
 
