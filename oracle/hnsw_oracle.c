@@ -72,6 +72,12 @@ static const float* row(const orc_graph* g, uint32_t i) { return g->data + (uint
 
 double orc_dist_to(const orc_graph* g, const float* q, uint32_t i) { return dist_vec(g, q, row(g, i)); }
 
+int orc_set_data(orc_graph* g, const float* data) {
+    if (!g || !data) return -1;
+    if (g->N * g->d) memcpy(g->data, data, sizeof(float) * g->N * g->d);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* binary heap over orc_item; is_max selects a max-heap (furthest on top)    */
 /* ------------------------------------------------------------------------ */

@@ -122,6 +122,11 @@ int orc_select_heuristic(const orc_graph* g, const float* base, uint32_t base_id
 /* Distance between a vector and data row i (fp64). */
 double orc_dist_to(const orc_graph* g, const float* q, uint32_t i);
 
+/* Replaces the N x d stored vectors, keeping every link: the same
+ * multilayer graph, searched over other coordinates (e.g. the dequantised
+ * rows of a lossy storage form).  Returns 0, or -1 for a null argument. */
+int orc_set_data(orc_graph* g, const float* data);
+
 /* Inspection. */
 uint64_t orc_n(const orc_graph* g);
 int orc_level(const orc_graph* g, uint32_t i);

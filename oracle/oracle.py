@@ -61,6 +61,7 @@ def lib():
                 "orc_select_simple": (i32, [vp, vp, vp, i32, i32, vp]),
                 "orc_select_heuristic": (i32, [vp, vp, u32, vp, i32, i32, i32, i32, i32, vp]),
                 "orc_dist_to": (f64, [vp, vp, u32]),
+                "orc_set_data": (i32, [vp, vp]),
                 "orc_n": (u64, [vp]),
                 "orc_level": (i32, [vp, u32]),
                 "orc_enter_point": (u32, [vp]),
@@ -144,6 +145,17 @@ class Graph:
         if r != 0:
             raise RuntimeError(f"orc_save_blob failed ({r})")
         return out.tobytes()
+
+    def with_data(self, data) -> "Graph":
+        """A copy of this graph (every link kept) over other N x d vectors."""
+        data = np.ascontiguousarray(data, dtype=np.float32)
+        if data.shape != self._data.shape:
+            raise ValueError("same N x d")
+        g = Graph.from_blob(self.to_blob())
+        if lib().orc_set_data(g.h, _p(data)) != 0:
+            raise RuntimeError("orc_set_data failed")
+        g._data = data
+        return g
 
     def __del__(self):
         if getattr(self, "h", None):

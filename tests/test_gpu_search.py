@@ -173,6 +173,25 @@ def test_quantised_with_rerank(H, storage):
     assert recall(gi, bi) >= recall(oi, bi) - 0.02
 
 
+@pytest.mark.parametrize("storage,name", [("fp8", "sift"), ("fp8", "glove"), ("bf16", "lowd"), ("f16", "lowd"),
+                                          ("bf16", "glove")])
+def test_quantised_distances_are_those_of_the_decoded_rows(H, storage, name):
+    # without rerank a quantised index returns distances to its decoded rows
+    # (round-to-nearest-even codes; fp8 with the row scale max|x| / 448): the
+    # oracle searches the same graph over the rows its own quantiser decodes
+    from oracle import quant_oracle as QO
+    g, X, blob = oracle_graph(name, 8000 if name == "glove" else 20_000)
+    h = g.with_data(QO.decoded_rows(storage, X))
+    Q = synth.queries(name, 300)
+    gi, gd = gpu_search(H, blob, Q, 10, 96, storage=storage)
+    oi, od, _ = oracle_batch(h, Q, 10, 96)
+    ex = np.array([[h.dist(Q[i], int(j)) for j in gi[i]] for i in range(len(Q))])
+    if name == "glove":  # cosine: compare the similarity 1 - d
+        gd, od, ex = 1.0 - gd.astype(np.float64), 1.0 - od, 1.0 - ex
+    np.testing.assert_allclose(gd, ex, rtol=1e-5, atol=0)
+    _tolerance_check(gi, gd, oi, od, overlap_min=0.995)
+
+
 def test_padding_when_fewer_than_k(H):
     from oracle import oracle as O
     X = synth.base("tiny", 7)
