@@ -254,6 +254,21 @@ def test_brute_force_against_numpy_sort(oracle):
     assert ds[0].tolist() == d[order].tolist()
 
 
+def test_brute_force_cosine_against_numpy(oracle):
+    # cosine distance 1 - <q, x> on unit vectors (Section 5.2): nearest = most similar
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((400, 16))
+    X = (X / np.linalg.norm(X, axis=1, keepdims=True)).astype(np.float32)
+    q = rng.standard_normal(16)
+    q = (q / np.linalg.norm(q)).astype(np.float32)[None, :]
+    ids, ds = oracle.brute_force(X, q, 15, metric=1)
+    sim = X.astype(np.float64) @ q[0].astype(np.float64)
+    order = np.argsort(-sim, kind="stable")[:15]
+    assert ids[0].tolist() == order.tolist()
+    np.testing.assert_allclose(ds[0], 1.0 - sim[order], rtol=0, atol=1e-12)
+    assert ds[0][0] >= 0.0 and np.all(np.diff(ds[0]) >= 0)
+
+
 # --------------------------------------------------------------------------
 # Alg. 3 (M nearest) and Alg. 4 (heuristic) properties
 # --------------------------------------------------------------------------
@@ -315,6 +330,29 @@ def test_heuristic_acceptance_properties(oracle):
                 continue
             earlier = [r for r in sel if order.index(r) < order.index(e)]
             assert any(dd(e, r) <= db[e] for r in earlier)
+
+
+def test_extend_candidates_adds_the_candidates_neighbourhoods(oracle):
+    # Alg. 4 lines 3-6: extendCandidates selects over C plus every layer-lc
+    # neighbour of an element of C (the base element itself excluded); the
+    # union is formed here from the graph's lists and selected without it
+    p = {"M": 6, "Mmax": 6, "Mmax0": 12, "efC": 40}
+    rng = np.random.default_rng(21)
+    X = rng.normal(size=(500, 5)).astype(np.float32)
+    g = oracle.Graph.build(X, 1.0 - rng.uniform(0.0, 1.0, 500), **p)  # u in (0, 1]
+    for t in range(15):
+        base_id = int(rng.integers(500))
+        cand = [int(c) for c in rng.choice(500, size=12, replace=False) if c != base_id]
+        union = list(cand)
+        for c in cand:
+            for a in g.neighbors(c, 0):
+                if a != base_id and a not in union:
+                    union.append(a)
+        assert len(union) > len(cand)
+        for keep in (False, True):
+            ext = g.select_heuristic(X[base_id], cand, 6, lc=0, base_id=base_id, extend=True, keep_pruned=keep)
+            ref = g.select_heuristic(X[base_id], union, 6, lc=0, base_id=base_id, keep_pruned=keep)
+            assert ext == ref
 
 
 def test_heuristic_bridges_clusters(oracle):
