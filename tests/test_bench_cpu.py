@@ -58,3 +58,56 @@ def test_threaded_oracle_runner_matches_one_thread():
     np.testing.assert_array_equal(a, b)
     assert list(bounds) == [0, 16, 32, 48, 64]
     assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
+
+
+def test_fp64_exact_knn_equals_the_oracle_on_tight_clusters():
+    # the low-d ground truth (fp64 expansion + fp64 rescoring), run with torch on the CPU
+    from oracle import oracle as O
+    X = synth.base("lowd", 5000)
+    Q = synth.queries("lowd", 64)
+    ids, _ = O.brute_force(X, Q, 10)
+    np.testing.assert_array_equal(bench.exact_knn_fp64(X, Q, 10, "cpu"), ids.astype(np.int64))
+
+
+def test_algorithmic_bytes_by_hand():
+    class Info:
+        row_bytes, storage, Mmax0, Mmax = 256, 1, 32, 16  # bf16 rows of 128 coordinates
+    stats = np.array([[1000, 60, 20], [500, 30, 10]], dtype=np.uint32)
+    # per query: rows + layer-0 lists (32 ids) + upper lists (16 ids + offset) + query + results
+    q0 = 1000 * 256 + 60 * 128 + 20 * 68 + 128 * 4 + 10 * 8
+    q1 = 500 * 256 + 30 * 128 + 10 * 68 + 128 * 4 + 10 * 8
+    total, m = bench.algorithmic_bytes(Info, stats, 10, 50, False, 128)
+    assert total == q0 + q1 and m["bytes_per_query"] == (q0 + q1) / 2
+    total, _ = bench.algorithmic_bytes(Info, stats, 10, 50, True, 128)  # + 50 fp32 rerank rows
+    assert total == q0 + q1 + 2 * 50 * 512
+
+    class Fp8:
+        row_bytes, storage, Mmax0, Mmax = 128, 2, 32, 16  # + the 4-byte row scale
+    total, _ = bench.algorithmic_bytes(Fp8, stats[:1], 10, 5, True, 128)  # ef' = max(ef, k) = 10
+    assert total == 1000 * 132 + 60 * 128 + 20 * 68 + 512 + 80 + 10 * 512
+
+
+def test_clock_samples_are_summarised(tmp_path):
+    c = bench.Clocks(0, enabled=False)
+    assert c.stop() is None
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self):
+            pass
+    c.p, c.path = Done(), str(tmp_path / "clocks.csv")
+    rows = ["0, 1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1100.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2010, 2070, 1180.5, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage"]
+    open(c.path, "w").write("\n".join(rows) + "\n")
+    s = c.stop()
+    assert s == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_traffic_counters_only_for_the_same_kernel_source():
+    traffic, sha = bench.load_traffic("no-such-kernel", 50)
+    assert traffic is None and len(sha) == 16
