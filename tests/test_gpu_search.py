@@ -57,6 +57,19 @@ def test_tiny_bit_exact(H, k, ef):
     np.testing.assert_array_equal(gs[:, 2], os_[:, 2])
 
 
+@pytest.mark.parametrize("k,ef", [(1024, 1024), (10, 1024), (1024, 1)])
+def test_tiny_bit_exact_at_the_limits(H, k, ef):
+    # the largest k and ef' = max(ef, k) the kernel takes (1024): W, the
+    # visited set (which overflows here) and the output at their maximum
+    g, X, blob = oracle_graph("tiny", 10_000)
+    Q = synth.queries("tiny", 200)
+    gi, gd, gs = gpu_search(H, blob, Q, k, ef, stats=True)
+    oi, od, os_ = oracle_batch(g, Q, k, ef)
+    np.testing.assert_array_equal(gi, oi)
+    np.testing.assert_array_equal(gd.astype(np.float64), od)
+    np.testing.assert_array_equal(gs[:, 1], os_[:, 1])
+
+
 def test_tiny_host_pointers_and_ragged(H):
     g, X, blob = oracle_graph("tiny", 10_000)
     Q = synth.queries("tiny", 77)  # not a multiple of the warps per block
