@@ -372,6 +372,30 @@ def test_heuristic_bridges_clusters(oracle):
     assert any(h >= 60 for h in heur)
 
 
+def test_heuristic_beats_simple_selection_on_clustered_data(oracle):
+    # Section 4 / Fig. 7: on strongly clustered low-dimensional data the
+    # M-nearest selection (Alg. 3) links only inside clusters and the search
+    # cannot leave the enter point's region; the heuristic (Alg. 4) keeps
+    # links between clusters
+    rng = np.random.default_rng(31)
+    centres = rng.uniform(0, 1, (50, 4))
+    X = (centres[rng.integers(0, 50, 5000)] + rng.normal(0, 0.003, (5000, 4))).astype(np.float32)
+    Q = (centres[rng.integers(0, 50, 300)] + rng.normal(0, 0.003, (300, 4))).astype(np.float32)
+    u = 1.0 - rng.uniform(0, 1, 5000)
+    gt, _ = oracle.brute_force(X, Q, 10)
+
+    def recall(g, ef):
+        ids, _ = g.knn_search_batch(Q, 10, ef)
+        return np.mean([len(set(ids[i].tolist()) & set(gt[i].tolist())) / 10 for i in range(len(Q))])
+
+    p = dict(M=6, Mmax=6, Mmax0=12, efC=40)
+    simple = oracle.Graph.build(X, u, heuristic=False, **p)
+    heur = oracle.Graph.build(X, u, heuristic=True, **p)
+    for ef in (10, 40):
+        rs, rh = recall(simple, ef), recall(heur, ef)
+        assert rh >= 0.98 and rh >= rs + 0.15, (ef, rs, rh)
+
+
 def test_heuristic_tie_is_rejected(oracle):
     # Alg. 4 line 11 read strictly: e with d(e,base) == d(e,r) is not "closer
     # to the base" than r, so it is discarded.
