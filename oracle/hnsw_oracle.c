@@ -74,7 +74,7 @@ double orc_dist_to(const orc_graph* g, const float* q, uint32_t i) { return dist
 
 int orc_set_data(orc_graph* g, const float* data) {
     if (!g || !data) return -1;
-    if (g->N * g->d) memcpy(g->data, data, sizeof(float) * g->N * g->d);
+    if (g->N && g->d) memcpy(g->data, data, sizeof(float) * g->N * g->d);
     return 0;
 }
 
@@ -498,6 +498,127 @@ int orc_build(orc_graph* g, const double* u) {
         if (r) return r;
     }
     return 0;
+}
+
+/* Alg. 1 with batched layer-0 insertions (see the header). */
+typedef struct {
+    uint32_t target, src, order;
+    double d;
+} orc_pair;
+
+static int cmp_pair(const void* x, const void* y) {
+    const orc_pair* a = (const orc_pair*)x;
+    const orc_pair* b = (const orc_pair*)y;
+    if (a->target != b->target) return a->target < b->target ? -1 : 1;
+    return a->order < b->order ? -1 : (a->order > b->order ? 1 : 0);
+}
+
+#define ORC_SHRINK_KEEP 256
+
+int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch) {
+    if (g->extend || g->n_inserted != 0) return -1;
+    const uint64_t N = g->N;
+    int* lv = (int*)malloc(sizeof(int) * (N > 0 ? N : 1));
+    uint32_t* rest = (uint32_t*)malloc(sizeof(uint32_t) * (N > 0 ? N : 1));
+    if (!lv || !rest) { free(lv); free(rest); return -1; }
+    uint64_t n_rest = 0, inserted = 0;
+    for (uint64_t i = 0; i < N; ++i) lv[i] = orc_level_from_u(u[i], g->mL);
+    /* the seed, in id order */
+    for (uint64_t i = 0; i < N; ++i) {
+        if (i < n_first || lv[i] > 0) {
+            if (orc_insert(g, (uint32_t)i, lv[i])) { free(lv); free(rest); return -1; }
+            ++inserted;
+        } else {
+            rest[n_rest++] = (uint32_t)i;
+        }
+    }
+    const int efc = (int)g->efC, M = (int)g->M;
+    const uint64_t bmax = n_rest < 64 ? 64 : (n_rest > 32768 ? 32768 : n_rest);
+    const uint64_t cap = batch ? batch : bmax;
+    uint32_t* rid = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(cap * efc + 1));
+    double* rd = (double*)malloc(sizeof(double) * (size_t)(cap * efc + 1));
+    orc_pair* pairs = (orc_pair*)malloc(sizeof(orc_pair) * (size_t)(cap * M + 1));
+    orc_item* C = (orc_item*)malloc(sizeof(orc_item) * (size_t)(efc + 1));
+    uint32_t* sel = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(g->Mmax0 + M + 1));
+    int rc = (rid && rd && pairs && C && sel) ? 0 : -1;
+    for (uint64_t pos = 0; rc == 0 && pos < n_rest;) {
+        uint64_t B = n_rest - pos;
+        if (batch) {
+            if (B > batch) B = batch;
+        } else {
+            const uint64_t grow = inserted / 16 > 64 ? inserted / 16 : 64;
+            if (B > bmax) B = bmax;
+            if (B > grow) B = grow;
+        }
+        /* 1. searches on the graph before the batch */
+        for (uint64_t b = 0; b < B; ++b)
+            if (orc_knn_search(g, row(g, rest[pos + b]), efc, efc, rid + b * efc, rd + b * efc, NULL)) rc = -1;
+        /* 2. forward links */
+        uint64_t np = 0;
+        for (uint64_t b = 0; rc == 0 && b < B; ++b) {
+            const uint32_t q = rest[pos + b];
+            int n = 0;
+            for (int i = 0; i < efc; ++i)
+                if (rid[b * efc + i] != ORC_NONE && rid[b * efc + i] != q) {
+                    C[n].id = rid[b * efc + i];
+                    C[n].d = rd[b * efc + i];
+                    ++n;
+                }
+            const int ns = select_items(g, row(g, q), q, C, n, M, 0, sel);
+            g->level[q] = 0;
+            g->n_inserted++;
+            uint32_t* ql = nbh(g, q, 0);
+            ql[0] = (uint32_t)ns;
+            for (int j = 0; j < ns; ++j) {
+                ql[1 + j] = sel[j];
+                pairs[np].target = sel[j];
+                pairs[np].src = q;
+                pairs[np].order = (uint32_t)np;
+                pairs[np].d = dist_vec(g, row(g, q), row(g, sel[j]));
+                ++np;
+            }
+        }
+        /* 3. reverse links, per target, new members in ascending id */
+        qsort(pairs, (size_t)np, sizeof(orc_pair), cmp_pair);
+        for (uint64_t i0 = 0; rc == 0 && i0 < np;) {
+            uint64_t i1 = i0 + 1;
+            while (i1 < np && pairs[i1].target == pairs[i0].target) ++i1;
+            const uint32_t e = pairs[i0].target;
+            uint32_t* el = nbh(g, e, 0);
+            const uint32_t n0 = el[0], nin = (uint32_t)(i1 - i0);
+            if (n0 + nin <= g->Mmax0) {
+                for (uint32_t t = 0; t < nin; ++t) el[1 + n0 + t] = pairs[i0 + t].src;
+                el[0] = n0 + nin;
+            } else {
+                orc_item* cand = (orc_item*)malloc(sizeof(orc_item) * (size_t)(n0 + nin));
+                uint32_t* out = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(g->Mmax0 + 1));
+                if (!cand || !out) {
+                    rc = -1;
+                } else {
+                    for (uint32_t j = 0; j < n0; ++j) {
+                        cand[j].id = el[1 + j];
+                        cand[j].d = dist_vec(g, row(g, e), row(g, el[1 + j]));
+                    }
+                    for (uint32_t t = 0; t < nin; ++t) {
+                        cand[n0 + t].id = pairs[i0 + t].src;
+                        cand[n0 + t].d = pairs[i0 + t].d;
+                    }
+                    qsort(cand, (size_t)(n0 + nin), sizeof(orc_item), cmp_item);
+                    const int nc = (int)(n0 + nin) < ORC_SHRINK_KEEP ? (int)(n0 + nin) : ORC_SHRINK_KEEP;
+                    const int nn = select_items(g, row(g, e), e, cand, nc, (int)g->Mmax0, 0, out);
+                    el[0] = (uint32_t)nn;
+                    for (int j = 0; j < nn; ++j) el[1 + j] = out[j];
+                }
+                free(cand);
+                free(out);
+            }
+            i0 = i1;
+        }
+        pos += B;
+        inserted += B;
+    }
+    free(lv); free(rest); free(rid); free(rd); free(pairs); free(C); free(sel);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -88,6 +88,25 @@ int orc_insert(orc_graph* g, uint32_t id, int level);
 /* Inserts elements 0..N-1 in order, element i at level orc_level_from_u(u[i], mL). */
 int orc_build(orc_graph* g, const double* u);
 
+/* Alg. 1 with the layer-0 insertions grouped in batches (the parallel
+ * construction of Section 4.1 in batch form).  Levels come from u as in
+ * orc_build.  The seed -- every element of level >= 1 and the elements with
+ * id < n_first -- is inserted first, in id order, by orc_insert.  The other
+ * elements (all of level 0) follow in id order, in batches of `batch`
+ * elements, or with batch = 0 of min(32768, max(64, remaining count at the
+ * start), remaining, max(64, inserted / 16)) elements.  For a batch:
+ *  1. every element q searches the graph as it stands before the batch:
+ *     Alg. 5 with K = ef = efConstruction (Alg. 1 lines 5-9 on layer 0);
+ *  2. q's layer-0 list becomes SELECT-NEIGHBORS(q, W, M) (line 10, lines
+ *     11's forward half), in selection order;
+ *  3. each element e selected by batch elements takes them into its list,
+ *     in ascending id: appended when they fit within Mmax0, otherwise the list
+ *     becomes SELECT-NEIGHBORS(e, old members + new ones, Mmax0) over the 256
+ *     candidates closest to e (lines 11-16).
+ * Elements of one batch do not see one another; batch = 1 is Alg. 1 applied
+ * in the order seed, then the rest.  extendCandidates must be off. */
+int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch);
+
 /* Alg. 5: K nearest of q; ids/dists have K slots; missing -> ORC_NONE/+inf. */
 int orc_knn_search(const orc_graph* g, const float* q, int K, int ef,
                    uint32_t* ids, double* dists, orc_stats* st);

@@ -55,6 +55,7 @@ def lib():
                 "orc_level_from_u": (i32, [f64, f64]),
                 "orc_insert": (i32, [vp, u32, i32]),
                 "orc_build": (i32, [vp, vp]),
+                "orc_build_batched": (i32, [vp, vp, u64, u32]),
                 "orc_knn_search": (i32, [vp, vp, i32, i32, vp, vp, vp]),
                 "orc_search_layer": (i32, [vp, vp, vp, i32, i32, i32, vp, vp, vp]),
                 "orc_greedy_layer": (u32, [vp, vp, u32, i32, vp]),
@@ -119,6 +120,19 @@ class Graph:
             raise ValueError("one u per element")
         if lib().orc_build(g.h, _p(u)) != 0:
             raise RuntimeError("orc_build failed")
+        return g
+
+    @classmethod
+    def build_batched(cls, data, u, n_first: int = 4096, batch: int = 0, **kw) -> "Graph":
+        """Alg. 1 with the layer-0 insertions in batches (orc_build_batched):
+        the seed (level >= 1 or id < n_first) first, then the others in
+        batches that search the graph as it stood before the batch."""
+        g = cls.new(data, **kw)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        if u.shape[0] != g._data.shape[0]:
+            raise ValueError("one u per element")
+        if lib().orc_build_batched(g.h, _p(u), int(n_first), int(batch)) != 0:
+            raise RuntimeError("orc_build_batched failed")
         return g
 
     def insert(self, i: int, level: int) -> None:

@@ -1,0 +1,114 @@
+"""Pins of the oracle's batched construction (orc_build_batched: Alg. 1 with
+the layer-0 insertions grouped in batches that search the graph as it stood
+before the batch, the batch form of Section 4.1's parallel construction):
+
+* with batches of one element it IS Alg. 1, applied in the order seed, then
+  the rest (byte-identical to orc_insert in that order), for Alg. 3, Alg. 4
+  and Alg. 4 with keepPrunedConnections, squared L2 and cosine;
+* with every element in the seed it is orc_build;
+* with the growing schedule, elements of one batch never link to one
+  another, the graph is valid, and its recall matches the sequential one's.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1603_09320_gb300 import synth
+
+
+def _levels(u, M):
+    return np.array([O.level_from_u(float(x), 1.0 / np.log(M)) for x in u])
+
+
+def _order(lv, n_first):
+    seed = [i for i in range(len(lv)) if i < n_first or lv[i] > 0]
+    rest = [i for i in range(len(lv)) if not (i < n_first or lv[i] > 0)]
+    return seed, rest
+
+
+def _schedule(n_seed, n_rest):
+    """Batch sizes of the growing schedule."""
+    bmax = min(32768, max(64, n_rest))
+    out, pos, inserted = [], 0, n_seed
+    while pos < n_rest:
+        b = min(bmax, n_rest - pos, max(64, inserted // 16))
+        out.append(b)
+        pos += b
+        inserted += b
+    return out
+
+
+@pytest.mark.parametrize("name,heuristic,keep", [("tiny", True, False), ("tiny", False, False),
+                                                 ("tiny", True, True), ("glove", True, False)])
+def test_batch_of_one_is_sequential_alg1(name, heuristic, keep):
+    p = dict(synth.params(name))
+    if name == "glove":
+        p["efC"] = 40
+    N = 2500
+    X = synth.base(name, N)
+    u = synth.level_uniforms(name, N)
+    gb = O.Graph.build_batched(X, u, n_first=300, batch=1, heuristic=heuristic, keep_pruned=keep, **p)
+    lv = _levels(u, p["M"])
+    seed, rest = _order(lv, 300)
+    gs = O.Graph.new(X, heuristic=heuristic, keep_pruned=keep, **p)
+    for i in seed + rest:
+        gs.insert(i, int(lv[i]))
+    assert gb.to_blob() == gs.to_blob()
+
+
+def test_all_seed_is_orc_build():
+    p = synth.params("tiny")
+    X = synth.base("tiny", 1500)
+    u = synth.level_uniforms("tiny", 1500)
+    assert O.Graph.build_batched(X, u, n_first=1500, **p).to_blob() == O.Graph.build(X, u, **p).to_blob()
+
+
+def test_growing_batches():
+    p = synth.params("tiny")
+    N = 8000
+    X = synth.base("tiny", N)
+    u = synth.level_uniforms("tiny", N)
+    n_first = 1000
+    g = O.Graph.build_batched(X, u, n_first=n_first, **p)
+    g = O.Graph.from_blob(g.to_blob())  # validating loader
+    lv = _levels(u, p["M"])
+    seed, rest = _order(lv, n_first)
+    sizes = _schedule(len(seed), len(rest))
+    assert sizes[0] == max(64, len(seed) // 16) and len(sizes) > 5 and sum(sizes) == len(rest)
+    batch_of = {}
+    pos = 0
+    for k, b in enumerate(sizes):
+        for i in rest[pos:pos + b]:
+            batch_of[i] = k
+        pos += b
+    for i in rest:  # no link inside a batch, in either direction
+        assert all(batch_of.get(j) != batch_of[i] for j in g.neighbors(i, 0))
+    for i in range(N):
+        nb = g.neighbors(i, 0)
+        assert 1 <= len(nb) <= p["Mmax0"] and i not in nb and len(set(nb)) == len(nb)
+    # upper layers: Alg. 1 over the seed, as in the sequential build of the seed
+    gs = O.Graph.new(X, **p)
+    for i in seed:
+        gs.insert(i, int(lv[i]))
+    assert g.enter_point == gs.enter_point and g.max_level == gs.max_level
+    for i in seed:
+        for lc in range(1, int(lv[i]) + 1):
+            assert g.neighbors(i, lc) == gs.neighbors(i, lc)
+    # as good a graph as sequential insertion
+    full = O.Graph.build(X, u, **p)
+    Q = synth.queries("tiny", 300)
+    gt, _ = O.brute_force(X, Q, 10)
+
+    def recall(h, ef):
+        ids, _ = h.knn_search_batch(Q, 10, ef)
+        return np.mean([len(set(ids[i].tolist()) & set(gt[i].tolist())) / 10 for i in range(len(Q))])
+
+    for ef in (16, 48):
+        assert recall(g, ef) >= recall(full, ef) - 0.02
+
+
+def test_extend_candidates_is_rejected():
+    p = synth.params("tiny")
+    X = synth.base("tiny", 200)
+    with pytest.raises(RuntimeError):
+        O.Graph.build_batched(X, synth.level_uniforms("tiny", 200), extend=True, **p)
