@@ -518,6 +518,7 @@ static int cmp_pair(const void* x, const void* y) {
 int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch) {
     if (g->extend || g->n_inserted != 0) return -1;
     const uint64_t N = g->N;
+    if (n_first < 1) n_first = 1;  /* the first element starts the graph (enter point) */
     int* lv = (int*)malloc(sizeof(int) * (N > 0 ? N : 1));
     uint32_t* rest = (uint32_t*)malloc(sizeof(uint32_t) * (N > 0 ? N : 1));
     if (!lv || !rest) { free(lv); free(rest); return -1; }

@@ -91,7 +91,7 @@ int orc_build(orc_graph* g, const double* u);
 /* Alg. 1 with the layer-0 insertions grouped in batches (the parallel
  * construction of Section 4.1 in batch form).  Levels come from u as in
  * orc_build.  The seed -- every element of level >= 1 and the elements with
- * id < n_first -- is inserted first, in id order, by orc_insert.  The other
+ * id < max(n_first, 1) -- is inserted first, in id order, by orc_insert.  The other
  * elements (all of level 0) follow in id order, in batches of `batch`
  * elements, or with batch = 0 of min(32768, max(64, remaining count at the
  * start), remaining, max(64, inserted / 16)) elements.  For a batch:

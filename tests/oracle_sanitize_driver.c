@@ -1,6 +1,6 @@
 /* Driver for the AddressSanitizer + UBSan build of the oracle
  * (oracle/hnsw_oracle.c), run by test_host_sanitizers.py: construction
- * (Alg. 1 with Alg. 3 / Alg. 4, both flags), the searches (Alg. 2, Alg. 5,
+ * (Alg. 1 with Alg. 3 / Alg. 4, both flags, sequential and in batches), the searches (Alg. 2, Alg. 5,
  * the traced form), the selection routines, brute force and the blob format
  * with its rejections, on small seeded inputs including the degenerate ones
  * (one element, K above N, ef = 1).  Exit status 0 when every call returned
@@ -90,6 +90,14 @@ static void run(uint64_t N, uint32_t d, int metric, int heuristic, int extend, i
     check(orc_load_blob(blob, 100, &err) == NULL, "short blob rejection");
     free(blob);
     orc_free(g);
+    if (!extend) { /* the batched construction, growing and fixed batches */
+        for (uint32_t batch = 0; batch < 8; batch += 7) {
+            orc_graph* b = orc_new(X, N, d, metric, 4, 4, 8, 24, 1.0 / log(4.0), heuristic, 0, keep);
+            check(b != NULL && orc_build_batched(b, u, N / 4, batch) == 0, "orc_build_batched");
+            if (b && N > 0) check(orc_knn_search(b, q, 10, 20, ids, ds, &st) == 0, "search of the batched graph");
+            orc_free(b);
+        }
+    }
 out:
     free(X);
     free(u);
