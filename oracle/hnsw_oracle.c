@@ -162,7 +162,7 @@ orc_graph* orc_new(const float* data, uint64_t N, uint32_t d, int metric,
     g->adj0 = (uint32_t*)calloc((N > 0 ? N : 1) * (Mmax0 + 2), sizeof(uint32_t));
     g->adjU = (uint32_t**)calloc(N > 0 ? N : 1, sizeof(uint32_t*));
     if (!g->data || !g->level || !g->adj0 || !g->adjU) { orc_free(g); return NULL; }
-    if (N * d) memcpy(g->data, data, sizeof(float) * N * d);
+    if (N && d) memcpy(g->data, data, sizeof(float) * N * d);
     for (uint64_t i = 0; i < N; ++i) g->level[i] = -1;
     g->ep = ORC_NONE;
     g->maxlevel = -1;
@@ -414,21 +414,11 @@ static int has_link(const uint32_t* list, uint32_t x) {
     return 0;
 }
 
-int orc_insert(orc_graph* g, uint32_t qid, int l) {
-    if (qid >= g->N || g->level[qid] >= 0 || l < 0 || l > 255) return -1;
+/* Alg. 1 lines 2-19 for element qid of level l (level and lists already
+ * set up), on layers lc >= lc_min only: lc_min = 0 is the whole insertion,
+ * lc_min = 1 the upper layers of an element already linked on layer 0. */
+static int insert_layers(orc_graph* g, uint32_t qid, int l, int lc_min) {
     const float* q = row(g, qid);
-    g->level[qid] = l;
-    if (l > 0) {
-        g->adjU[qid] = (uint32_t*)calloc((size_t)l * (g->Mmax + 2), sizeof(uint32_t));
-        if (!g->adjU[qid]) return -1;
-    }
-    /* the first element: it becomes the enter point, no links */
-    if (g->n_inserted == 0) {
-        g->ep = qid;
-        g->maxlevel = l;
-        g->n_inserted = 1;
-        return 0;
-    }
     int cap_w = (int)g->efC + 2;
     orc_item* W = (orc_item*)malloc(sizeof(orc_item) * (size_t)cap_w);
     orc_item* ep = (orc_item*)malloc(sizeof(orc_item) * (size_t)cap_w);
@@ -449,7 +439,7 @@ int orc_insert(orc_graph* g, uint32_t qid, int l) {
         (void)n;
     }
     /* lines 8-17 */
-    for (int lc = (L < l ? L : l); lc >= 0; --lc) {
+    for (int lc = (L < l ? L : l); lc >= lc_min; --lc) {
         int nW = search_layer_items(g, q, ep, n_ep, (int)g->efC, lc, W, NULL);  /* line 9 */
         for (int i = 0; i < nW; ++i) cand[i] = W[i];
         int nsel = select_items(g, q, qid, cand, nW, (int)g->M, lc, sel);         /* line 10 */
@@ -487,8 +477,31 @@ int orc_insert(orc_graph* g, uint32_t qid, int l) {
         g->ep = qid;
         g->maxlevel = l;
     }
-    g->n_inserted++;
     free(W); free(ep); free(cand); free(sel);
+    return 0;
+}
+
+static int alloc_upper(orc_graph* g, uint32_t qid, int l) {
+    g->level[qid] = l;
+    if (l > 0) {
+        g->adjU[qid] = (uint32_t*)calloc((size_t)l * (g->Mmax + 2), sizeof(uint32_t));
+        if (!g->adjU[qid]) return -1;
+    }
+    return 0;
+}
+
+int orc_insert(orc_graph* g, uint32_t qid, int l) {
+    if (qid >= g->N || g->level[qid] >= 0 || l < 0 || l > 255) return -1;
+    if (alloc_upper(g, qid, l)) return -1;
+    /* the first element: it becomes the enter point, no links */
+    if (g->n_inserted == 0) {
+        g->ep = qid;
+        g->maxlevel = l;
+        g->n_inserted = 1;
+        return 0;
+    }
+    if (insert_layers(g, qid, l, 0)) return -1;
+    g->n_inserted++;
     return 0;
 }
 
@@ -515,26 +528,11 @@ static int cmp_pair(const void* x, const void* y) {
 
 #define ORC_SHRINK_KEEP 256
 
-int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch) {
-    if (g->extend || g->n_inserted != 0) return -1;
-    const uint64_t N = g->N;
-    if (n_first < 1) n_first = 1;  /* the first element starts the graph (enter point) */
-    int* lv = (int*)malloc(sizeof(int) * (N > 0 ? N : 1));
-    uint32_t* rest = (uint32_t*)malloc(sizeof(uint32_t) * (N > 0 ? N : 1));
-    if (!lv || !rest) { free(lv); free(rest); return -1; }
-    uint64_t n_rest = 0, inserted = 0;
-    for (uint64_t i = 0; i < N; ++i) lv[i] = orc_level_from_u(u[i], g->mL);
-    /* the seed, in id order */
-    for (uint64_t i = 0; i < N; ++i) {
-        if (i < n_first || lv[i] > 0) {
-            if (orc_insert(g, (uint32_t)i, lv[i])) { free(lv); free(rest); return -1; }
-            ++inserted;
-        } else {
-            rest[n_rest++] = (uint32_t)i;
-        }
-    }
+/* Layer-0 insertion of ids[0..n_ids) (id order, none inserted yet) in
+ * batches: `inserted` elements are in the graph before the first batch. */
+static int layer0_batches(orc_graph* g, const uint32_t* ids, uint64_t n_ids, uint64_t inserted, uint32_t batch) {
     const int efc = (int)g->efC, M = (int)g->M;
-    const uint64_t bmax = n_rest < 64 ? 64 : (n_rest > 32768 ? 32768 : n_rest);
+    const uint64_t bmax = n_ids < 64 ? 64 : (n_ids > 32768 ? 32768 : n_ids);
     const uint64_t cap = batch ? batch : bmax;
     uint32_t* rid = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(cap * efc + 1));
     double* rd = (double*)malloc(sizeof(double) * (size_t)(cap * efc + 1));
@@ -542,8 +540,8 @@ int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t 
     orc_item* C = (orc_item*)malloc(sizeof(orc_item) * (size_t)(efc + 1));
     uint32_t* sel = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(g->Mmax0 + M + 1));
     int rc = (rid && rd && pairs && C && sel) ? 0 : -1;
-    for (uint64_t pos = 0; rc == 0 && pos < n_rest;) {
-        uint64_t B = n_rest - pos;
+    for (uint64_t pos = 0; rc == 0 && pos < n_ids;) {
+        uint64_t B = n_ids - pos;
         if (batch) {
             if (B > batch) B = batch;
         } else {
@@ -553,11 +551,11 @@ int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t 
         }
         /* 1. searches on the graph before the batch */
         for (uint64_t b = 0; b < B; ++b)
-            if (orc_knn_search(g, row(g, rest[pos + b]), efc, efc, rid + b * efc, rd + b * efc, NULL)) rc = -1;
+            if (orc_knn_search(g, row(g, ids[pos + b]), efc, efc, rid + b * efc, rd + b * efc, NULL)) rc = -1;
         /* 2. forward links */
         uint64_t np = 0;
         for (uint64_t b = 0; rc == 0 && b < B; ++b) {
-            const uint32_t q = rest[pos + b];
+            const uint32_t q = ids[pos + b];
             int n = 0;
             for (int i = 0; i < efc; ++i)
                 if (rid[b * efc + i] != ORC_NONE && rid[b * efc + i] != q) {
@@ -618,7 +616,60 @@ int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t 
         pos += B;
         inserted += B;
     }
-    free(lv); free(rest); free(rid); free(rd); free(pairs); free(C); free(sel);
+    free(rid); free(rd); free(pairs); free(C); free(sel);
+    return rc;
+}
+
+int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch) {
+    if (g->extend || g->n_inserted != 0) return -1;
+    const uint64_t N = g->N;
+    if (n_first < 1) n_first = 1;  /* the first element starts the graph (enter point) */
+    int* lv = (int*)malloc(sizeof(int) * (N > 0 ? N : 1));
+    uint32_t* rest = (uint32_t*)malloc(sizeof(uint32_t) * (N > 0 ? N : 1));
+    if (!lv || !rest) { free(lv); free(rest); return -1; }
+    uint64_t n_rest = 0, inserted = 0;
+    for (uint64_t i = 0; i < N; ++i) lv[i] = orc_level_from_u(u[i], g->mL);
+    /* the seed, in id order */
+    for (uint64_t i = 0; i < N; ++i) {
+        if (i < n_first || lv[i] > 0) {
+            if (orc_insert(g, (uint32_t)i, lv[i])) { free(lv); free(rest); return -1; }
+            ++inserted;
+        } else {
+            rest[n_rest++] = (uint32_t)i;
+        }
+    }
+    const int rc = layer0_batches(g, rest, n_rest, inserted, batch);
+    free(lv); free(rest);
+    return rc;
+}
+
+int orc_insert_batched(orc_graph* g, const double* u, uint64_t first, uint64_t n, uint32_t batch) {
+    if (g->extend || g->n_inserted != first || first + n > g->N || first == 0) return -1;
+    for (uint64_t i = first; i < first + n; ++i)
+        if (g->level[i] >= 0) return -1;
+    uint32_t* U = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+    uint32_t* Z = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+    int* lv = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+    if (!U || !Z || !lv) { free(U); free(Z); free(lv); return -1; }
+    uint64_t nu = 0, nz = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        lv[i] = orc_level_from_u(u[i], g->mL);
+        if (lv[i] > 255) { free(U); free(Z); free(lv); return -1; }
+        if (lv[i] > 0) U[nu++] = (uint32_t)(first + i);
+        else Z[nz++] = (uint32_t)(first + i);
+    }
+    /* 1. layer 0 of the new elements of level >= 1, through the upper layers
+     *    as they stand (the new elements are not on them yet) */
+    int rc = layer0_batches(g, U, nu, first, batch);
+    /* 2. their upper layers, one at a time in id order (Alg. 1 on lc >= 1) */
+    for (uint64_t j = 0; rc == 0 && j < nu; ++j) {
+        const uint32_t q = U[j];
+        const int l = lv[q - first];
+        if (alloc_upper(g, q, l) || insert_layers(g, q, l, 1)) rc = -1;
+    }
+    /* 3. layer 0 of the new elements of level 0 */
+    if (rc == 0) rc = layer0_batches(g, Z, nz, first + nu, batch);
+    free(U); free(Z); free(lv);
     return rc;
 }
 

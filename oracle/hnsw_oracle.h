@@ -107,6 +107,17 @@ int orc_build(orc_graph* g, const double* u);
  * in the order seed, then the rest.  extendCandidates must be off. */
 int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch);
 
+/* Incremental insertion of elements first..first+n-1 (rows of the data, not
+ * inserted yet) into a graph holding exactly elements 0..first-1, levels
+ * from u[0..n): 1. the new elements of level >= 1 take their layer-0 links
+ * in batches as in orc_build_batched, searching through the upper layers as
+ * they stand; 2. their upper layers follow one at a time in id order (Alg. 1
+ * on layers >= 1, enter point updated by lines 18-19); 3. the new elements of
+ * level 0 are inserted on layer 0 in batches.  Batches as in
+ * orc_build_batched (0: the growing schedule, starting from the elements
+ * present). */
+int orc_insert_batched(orc_graph* g, const double* u, uint64_t first, uint64_t n, uint32_t batch);
+
 /* Alg. 5: K nearest of q; ids/dists have K slots; missing -> ORC_NONE/+inf. */
 int orc_knn_search(const orc_graph* g, const float* q, int K, int ef,
                    uint32_t* ids, double* dists, orc_stats* st);

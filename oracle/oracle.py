@@ -56,6 +56,7 @@ def lib():
                 "orc_insert": (i32, [vp, u32, i32]),
                 "orc_build": (i32, [vp, vp]),
                 "orc_build_batched": (i32, [vp, vp, u64, u32]),
+                "orc_insert_batched": (i32, [vp, vp, u64, u64, u32]),
                 "orc_knn_search": (i32, [vp, vp, i32, i32, vp, vp, vp]),
                 "orc_search_layer": (i32, [vp, vp, vp, i32, i32, i32, vp, vp, vp]),
                 "orc_greedy_layer": (u32, [vp, vp, u32, i32, vp]),
@@ -134,6 +135,12 @@ class Graph:
         if lib().orc_build_batched(g.h, _p(u), int(n_first), int(batch)) != 0:
             raise RuntimeError("orc_build_batched failed")
         return g
+
+    def insert_batched(self, first: int, u, batch: int = 0) -> None:
+        """orc_insert_batched: elements first .. first + len(u) - 1."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        if lib().orc_insert_batched(self.h, _p(u), int(first), int(u.shape[0]), int(batch)) != 0:
+            raise RuntimeError("orc_insert_batched failed")
 
     def insert(self, i: int, level: int) -> None:
         if lib().orc_insert(self.h, i, level) != 0:

@@ -96,6 +96,18 @@ static void run(uint64_t N, uint32_t d, int metric, int heuristic, int extend, i
             check(b != NULL && orc_build_batched(b, u, N / 4, batch) == 0, "orc_build_batched");
             if (b && N > 0) check(orc_knn_search(b, q, 10, 20, ids, ds, &st) == 0, "search of the batched graph");
             orc_free(b);
+            /* incremental: the first half in sequence, the rest in two insertions */
+            if (N >= 4) {
+                orc_graph* c = orc_new(X, N, d, metric, 4, 4, 8, 24, 1.0 / log(4.0), heuristic, 0, keep);
+                check(c != NULL, "orc_new (incremental)");
+                if (!c) continue;
+                const uint64_t h = N / 2, m = h + (N - h) / 2;
+                for (uint64_t i = 0; i < h; ++i) check(orc_insert(c, (uint32_t)i, orc_level_from_u(u[i], 1.0 / log(4.0))) == 0, "seed");
+                check(orc_insert_batched(c, u + h, h, m - h, batch) == 0, "orc_insert_batched");
+                check(orc_insert_batched(c, u + m, m, N - m, batch) == 0, "orc_insert_batched (second)");
+                check(orc_insert_batched(c, u, 1, 1, batch) != 0, "insertion of present elements rejected");
+                orc_free(c);
+            }
         }
     }
 out:

@@ -112,3 +112,68 @@ def test_extend_candidates_is_rejected():
     X = synth.base("tiny", 200)
     with pytest.raises(RuntimeError):
         O.Graph.build_batched(X, synth.level_uniforms("tiny", 200), extend=True, **p)
+
+
+def _sequential(X, u, n0, p):
+    lv = _levels(u, p["M"])
+    g = O.Graph.new(X, **p)
+    for i in range(n0):
+        g.insert(i, int(lv[i]))
+    return g, lv
+
+
+def test_incremental_level0_batch_of_one_is_sequential_alg1():
+    # new elements all of level 0 (u = 1): batches of one are Alg. 1 in id order
+    p = synth.params("tiny")
+    N, n0 = 3000, 1200
+    X = synth.base("tiny", N)
+    u = synth.level_uniforms("tiny", N).copy()
+    u[n0:] = 1.0
+    g, lv = _sequential(X, u, n0, p)
+    g.insert_batched(n0, u[n0:2000], batch=1)
+    g.insert_batched(2000, u[2000:], batch=1)
+    ref = O.Graph.build(X, u, **p)
+    assert g.to_blob() == ref.to_blob()
+
+
+def test_incremental_upper_layers_are_sequential_alg1():
+    # levels >= 1 among the new elements: their upper layers are Alg. 1 over
+    # all elements in id order (layers >= 1 involve only elements of level >= 1)
+    p = synth.params("tiny")
+    N, n0 = 6000, 2500
+    X = synth.base("tiny", N)
+    u = synth.level_uniforms("tiny", N)
+    g, lv = _sequential(X, u, n0, p)
+    for lo, hi in ((n0, 4000), (4000, N)):
+        g.insert_batched(lo, u[lo:hi])
+    g = O.Graph.from_blob(g.to_blob())
+    full = O.Graph.build(X, u, **p)
+    assert g.enter_point == full.enter_point and g.max_level == full.max_level
+    assert np.array_equal(g.levels(), full.levels())
+    for i in np.nonzero(lv > 0)[0]:
+        for lc in range(1, int(lv[i]) + 1):
+            assert g.neighbors(int(i), lc) == full.neighbors(int(i), lc)
+    for i in range(N):
+        nb = g.neighbors(i, 0)
+        assert 1 <= len(nb) <= p["Mmax0"] and i not in nb and len(set(nb)) == len(nb)
+    Q = synth.queries("tiny", 300)
+    gt, _ = O.brute_force(X, Q, 10)
+    for ef in (16, 48):
+        r = [np.mean([len(set(ids[i].tolist()) & set(gt[i].tolist())) / 10 for i in range(len(Q))])
+             for ids in (h.knn_search_batch(Q, 10, ef)[0] for h in (g, full))]
+        assert r[0] >= r[1] - 0.02
+
+
+def test_incremental_rejects_bad_ranges():
+    p = synth.params("tiny")
+    X = synth.base("tiny", 500)
+    u = synth.level_uniforms("tiny", 500)
+    g, _ = _sequential(X, u, 300, p)
+    with pytest.raises(RuntimeError):
+        g.insert_batched(200, u[200:300])  # already inserted
+    with pytest.raises(RuntimeError):
+        g.insert_batched(350, u[350:400])  # not contiguous with the graph
+    with pytest.raises(RuntimeError):
+        g.insert_batched(300, np.ones(300))  # beyond the rows
+    g.insert_batched(300, u[300:500])
+    assert g.N == 500
