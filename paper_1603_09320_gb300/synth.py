@@ -106,7 +106,10 @@ class _LowdMixture:
 
 
 def base(name: str, n: int | None = None) -> np.ndarray:
-    """Base vectors of a workload (first n rows of the full-size draw order)."""
+    """n base vectors of a workload (default: its full size).  Rows are drawn
+    in chunks (65,536 rows; 262,144 for lowd), so the first whole chunks of a
+    smaller draw equal those of the full-size one; the rows after the last
+    whole chunk follow the same distribution but are other draws."""
     idx, N, d, *_ = WORKLOADS[name]
     n = N if n is None else n
     seed = 1000 + idx
