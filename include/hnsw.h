@@ -211,6 +211,8 @@ typedef struct {
     uint64_t device_bytes;
 } hnsw_index_info;
 
+/* Copies the index's shape and sizes into *out (host).  Never touches the
+ * device.  Errors: HNSW_EINVAL (null pointer). */
 hnsw_status hnsw_get_index_info(const hnsw_index* index, hnsw_index_info* out);
 
 /* ------------------------------------------------------------------------ */
@@ -265,7 +267,10 @@ typedef struct {
 } hnsw_search_params;
 
 /* hnsw_search with the options above and optional per-query counters
- * (stats may be NULL; host or device memory, [n]). */
+ * (stats may be NULL; host or device memory, [n]).  Same memory and stream
+ * rules as hnsw_search.  Errors: those of hnsw_search; HNSW_EINVAL also for a
+ * null params, visited_log2 outside [5,15] (when not 0), rerank without the
+ * fp32 copy, stop_period above 65535. */
 hnsw_status hnsw_search_ex(hnsw_index* index, const hnsw_search_params* params,
                            const float* queries, int64_t n, uint32_t* out_ids, float* out_dists,
                            hnsw_query_stats* stats, void* stream);
@@ -286,7 +291,10 @@ hnsw_status hnsw_search_ex(hnsw_index* index, const hnsw_search_params* params,
  * (x - mean) / std before the first layer. */
 #define HNSW_STOP_NPARAM 4673
 
-/* Installs (or replaces) the index's stop network; host arrays. */
+/* Installs (or replaces) the index's stop network; host arrays, copied.
+ * Errors: HNSW_EINVAL (null argument, a std <= 0), HNSW_ENOMEM, HNSW_ECUDA.
+ * hnsw_clear_stop_model removes it (searches with a threshold then run the
+ * plain search); HNSW_EINVAL for a null index. */
 hnsw_status hnsw_set_stop_model(hnsw_index* index, const float* norm12, const uint16_t* w_fp16);
 hnsw_status hnsw_clear_stop_model(hnsw_index* index);
 
@@ -296,7 +304,10 @@ hnsw_status hnsw_clear_stop_model(hnsw_index* index);
  * k into topk[n][max_checks][k] and, when logits is not NULL and the index
  * has a stop network, its logit into logits[n][max_checks]; n_checks[n]
  * receives the number of checks recorded (at most max_checks).  All buffers
- * are device memory; asynchronous on stream. */
+ * are device memory; asynchronous on stream.  Errors: HNSW_EINVAL (null
+ * index or params, n < 0, max_checks < 1, k or ef out of range as in
+ * hnsw_search, host buffers, rerank without the fp32 copy, stop_period above
+ * 65535), HNSW_ECUDA. */
 hnsw_status hnsw_search_trace(hnsw_index* index, const hnsw_search_params* params, const float* queries,
                               int64_t n, int32_t max_checks, float* feats, uint32_t* topk, float* logits,
                               int32_t* n_checks, uint32_t* out_ids, float* out_dists,
@@ -305,7 +316,8 @@ hnsw_status hnsw_search_trace(hnsw_index* index, const hnsw_search_params* param
 /* Gradient of the mean binary cross-entropy of the network over n samples
  * (x: device [n][6] raw features, y: device [n] labels in {0,1}) at the given
  * fp16 weights and normalisation (host); writes grad_out[4673] and the mean
- * loss (host).  Synchronous. */
+ * loss (host).  Synchronous.  Errors: HNSW_EINVAL (null argument, n < 1, x or
+ * y not device memory), HNSW_ENOMEM, HNSW_ECUDA. */
 hnsw_status hnsw_stop_grad(const float* x, const float* y, int64_t n, const float* norm12,
                            const uint16_t* w_fp16, float* grad_out, float* loss_out, void* stream);
 
@@ -322,7 +334,9 @@ typedef struct {
  * the samples' mean and std, then epochs of Adam on fp32 master weights with
  * fp16 working weights.  Writes norm_out[12], w_out[4673] (host) and, when
  * not NULL, the mean loss of every epoch.  x, y: device memory as in
- * hnsw_stop_grad.  Synchronous. */
+ * hnsw_stop_grad.  Synchronous.  Errors: HNSW_EINVAL (null argument, n < 1,
+ * epochs < 1, batch not a positive multiple of 128, lr <= 0, x or y not
+ * device memory), HNSW_ENOMEM, HNSW_ECUDA. */
 hnsw_status hnsw_stop_train(const float* x, const float* y, int64_t n, const hnsw_stop_train_params* params,
                             const uint16_t* w_init, float* norm_out, uint16_t* w_out, float* loss_per_epoch,
                             void* stream);
