@@ -1,6 +1,7 @@
 """hnsw_build_gpu: the seed built on the host, layer 0 of the other elements
 built on the GPU in batches.  Parity with sequential insertion is unpinned
-(batch-parallel insertion); what is pinned:
+(batch-parallel insertion; parity with the oracle's batch form is checked
+byte for byte in test_gpu_build_exact.py); what is pinned here:
 
 * the upper layers and the enter point equal the oracle's Alg. 1 run over the
   seed (every element of level >= 1 and the first 4,096, in id order), since

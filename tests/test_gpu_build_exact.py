@@ -2,17 +2,15 @@
 forms (orc_build_batched, orc_insert_batched: Alg. 1 with layer-0
 insertions in batches that search the graph as it stood before the batch,
 pinned on the CPU to Alg. 1 at batch size one), byte for byte on integer
-data, where the kernels' fp32 distances are exact.
-
-Marked xfail (not strict) until the comparison has run on a GPU: a mismatch
-is reported without stopping the suite, a pass shows as XPASS."""
+data, where the kernels' fp32 distances are exact: bulk construction with
+Alg. 3, Alg. 4 and Alg. 4 with keepPrunedConnections, and two incremental
+insertions into a resident index."""
 import numpy as np
 import pytest
 
 from paper_1603_09320_gb300 import synth
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.xfail(strict=False, reason="comparison with the batched oracle not yet run on a GPU")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("heuristic,keep", [(True, False), (False, False), (True, True)])

@@ -8,9 +8,10 @@ Pinned against the oracle:
   all elements, list by list: layers >= 1 only involve elements of level
   >= 1 in id order, which the insertion processes one at a time exactly as
   Alg. 1 does (integer-valued data: fp32 distances are exact);
-* layer 0 (batch insertion, parity unpinned) passes the validating loader,
-  keeps the caps, and reaches the oracle graph's reachability and recall
-  within a small margin.
+* layer 0 (batch insertion) passes the validating loader, keeps the caps,
+  and reaches the oracle graph's reachability and recall within a small
+  margin; its byte-for-byte parity with the oracle's batch form is checked in
+  test_gpu_build_exact.py.
 Concurrent searches during insertion return valid results, and afterwards
 the live index searches exactly like a fresh upload of its own blob.
 """
