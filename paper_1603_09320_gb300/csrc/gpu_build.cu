@@ -20,8 +20,9 @@
 // inserted, so each element searches a graph that already holds at least 94%
 // of what precedes it.  The insertion order is a permutation of Alg. 1's (seed
 // first) with batch-parallel semantics, so the graph is not the sequential
-// one: like the multi-threaded host builder it is checked by invariants and
-// recall, not element by element.
+// one; it is deterministic, and on integer data equal byte for byte to the
+// oracle's batch form of Alg. 1 (which batches of one element reduce to
+// Alg. 1 itself).
 #include <cub/cub.cuh>
 #include <cuda_runtime.h>
 
