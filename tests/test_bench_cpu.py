@@ -111,3 +111,25 @@ def test_clock_samples_are_summarised(tmp_path):
 def test_traffic_counters_only_for_the_same_kernel_source():
     traffic, sha = bench.load_traffic("no-such-kernel", 50)
     assert traffic is None and len(sha) == 16
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the reference arm runs the oracle on the host cores only: run it end to
+    # end on a small base and check its JSON line
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n-base", "5000",
+                        "--n-queries", "1000", "--batches", "5", "--steps", "2", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-3000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "queries/s"
+    assert (line["n_gpus"], line["steps"], line["warmup"], line["higher_is_better"]) == (1, 2, 1, True)
+    assert line["vs_baseline"] is None and "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "queries/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
