@@ -88,6 +88,28 @@ def test_hand_example_search(oracle):
     assert ds.tolist() == h["search_k1_ef1"]["dists"]
 
 
+def test_hand_example_trace(oracle):
+    # The layer-0 beam of the search above (K=2, ef=2, from p3 at 85), state
+    # after each expansion (Alg. 2 lines 4-17):
+    #   expand p3: p1 (5) joins W, p2 (225) rejected -> W {p1, p3}; 2 evals;
+    #              K-th nearest p3 (85) is the first -> stale 0
+    #   expand p1: p4 (65) joins, p3 evicted; p5 (65,5) loses to (65,4)
+    #              -> W {p1, p4}; 4 evals; K-th improves to p4 -> stale 0
+    #   expand p4: p0 (145) rejected -> W unchanged; 5 evals; stale 1
+    # With a record every T=2 expansions only the second state is kept.
+    h = _hand()
+    X = np.array(h["points"], dtype=np.float32)
+    p = h["params"]
+    g = oracle.Graph.new(X, metric=0, M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"], efC=p["efC"])
+    for i, l in enumerate(h["levels"]):
+        g.insert(i, l)
+    q = np.array(h["query"], dtype=np.float32)
+    for T, key in ((1, "T1"), (2, "T2")):
+        raw, topk = g.knn_search_trace(q, 2, 2, T=T)
+        e = h["trace_k2_ef2"][key]
+        assert raw.tolist() == e["raw"] and topk.tolist() == e["topk"]
+
+
 # --------------------------------------------------------------------------
 # Level distribution (Alg. 1 line 4; Section 4.1 mL = 1/ln M; eq. (1))
 # --------------------------------------------------------------------------
