@@ -526,23 +526,33 @@ static int cmp_pair(const void* x, const void* y) {
     return a->order < b->order ? -1 : (a->order > b->order ? 1 : 0);
 }
 
-#define ORC_SHRINK_KEEP 256
-
 /* Layer-0 insertion of ids[0..n_ids) (id order, none inserted yet) in
- * batches: `inserted` elements are in the graph before the first batch. */
-static int layer0_batches(orc_graph* g, const uint32_t* ids, uint64_t n_ids, uint64_t inserted, uint32_t batch) {
+ * batches: `inserted` elements are in the graph before the first batch.
+ * Batch sizes: sizes[0..n_sizes) when given (the last one repeated, each
+ * clipped to what remains), else `batch`, else the growing schedule. */
+static int layer0_batches(orc_graph* g, const uint32_t* ids, uint64_t n_ids, uint64_t inserted, uint32_t batch,
+                          const uint32_t* sizes, uint64_t n_sizes) {
     const int efc = (int)g->efC, M = (int)g->M;
     const uint64_t bmax = n_ids < 64 ? 64 : (n_ids > 32768 ? 32768 : n_ids);
-    const uint64_t cap = batch ? batch : bmax;
+    uint64_t cap = batch ? batch : bmax;
+    if (sizes && n_sizes) {
+        cap = 1;
+        for (uint64_t j = 0; j < n_sizes; ++j)
+            if (sizes[j] > cap) cap = sizes[j];
+    }
     uint32_t* rid = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(cap * efc + 1));
     double* rd = (double*)malloc(sizeof(double) * (size_t)(cap * efc + 1));
     orc_pair* pairs = (orc_pair*)malloc(sizeof(orc_pair) * (size_t)(cap * M + 1));
     orc_item* C = (orc_item*)malloc(sizeof(orc_item) * (size_t)(efc + 1));
     uint32_t* sel = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(g->Mmax0 + M + 1));
     int rc = (rid && rd && pairs && C && sel) ? 0 : -1;
-    for (uint64_t pos = 0; rc == 0 && pos < n_ids;) {
+    for (uint64_t pos = 0, nb = 0; rc == 0 && pos < n_ids; ++nb) {
         uint64_t B = n_ids - pos;
-        if (batch) {
+        if (sizes && n_sizes) {
+            const uint64_t want = sizes[nb < n_sizes ? nb : n_sizes - 1];
+            if (want == 0) { rc = -1; break; }
+            if (B > want) B = want;
+        } else if (batch) {
             if (B > batch) B = batch;
         } else {
             const uint64_t grow = inserted / 16 > 64 ? inserted / 16 : 64;
@@ -602,9 +612,10 @@ static int layer0_batches(orc_graph* g, const uint32_t* ids, uint64_t n_ids, uin
                         cand[n0 + t].id = pairs[i0 + t].src;
                         cand[n0 + t].d = pairs[i0 + t].d;
                     }
+                    /* Alg. 1 lines 13-15: SELECT-NEIGHBORS(e, eConn, Mmax0) over
+                     * the whole of eConn, old members and new ones */
                     qsort(cand, (size_t)(n0 + nin), sizeof(orc_item), cmp_item);
-                    const int nc = (int)(n0 + nin) < ORC_SHRINK_KEEP ? (int)(n0 + nin) : ORC_SHRINK_KEEP;
-                    const int nn = select_items(g, row(g, e), e, cand, nc, (int)g->Mmax0, 0, out);
+                    const int nn = select_items(g, row(g, e), e, cand, (int)(n0 + nin), (int)g->Mmax0, 0, out);
                     el[0] = (uint32_t)nn;
                     for (int j = 0; j < nn; ++j) el[1 + j] = out[j];
                 }
@@ -620,7 +631,8 @@ static int layer0_batches(orc_graph* g, const uint32_t* ids, uint64_t n_ids, uin
     return rc;
 }
 
-int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch) {
+static int build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch, const uint32_t* sizes,
+                         uint64_t n_sizes) {
     if (g->extend || g->n_inserted != 0) return -1;
     const uint64_t N = g->N;
     if (n_first < 1) n_first = 1;  /* the first element starts the graph (enter point) */
@@ -638,9 +650,19 @@ int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t 
             rest[n_rest++] = (uint32_t)i;
         }
     }
-    const int rc = layer0_batches(g, rest, n_rest, inserted, batch);
+    const int rc = layer0_batches(g, rest, n_rest, inserted, batch, sizes, n_sizes);
     free(lv); free(rest);
     return rc;
+}
+
+int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch) {
+    return build_batched(g, u, n_first, batch, NULL, 0);
+}
+
+int orc_build_batched_sizes(orc_graph* g, const double* u, uint64_t n_first, const uint32_t* sizes,
+                            uint64_t n_sizes) {
+    if (!sizes || n_sizes == 0) return -1;
+    return build_batched(g, u, n_first, 0, sizes, n_sizes);
 }
 
 int orc_insert_batched(orc_graph* g, const double* u, uint64_t first, uint64_t n, uint32_t batch) {
@@ -660,7 +682,7 @@ int orc_insert_batched(orc_graph* g, const double* u, uint64_t first, uint64_t n
     }
     /* 1. layer 0 of the new elements of level >= 1, through the upper layers
      *    as they stand (the new elements are not on them yet) */
-    int rc = layer0_batches(g, U, nu, first, batch);
+    int rc = layer0_batches(g, U, nu, first, batch, NULL, 0);
     /* 2. their upper layers, one at a time in id order (Alg. 1 on lc >= 1) */
     for (uint64_t j = 0; rc == 0 && j < nu; ++j) {
         const uint32_t q = U[j];
@@ -668,7 +690,7 @@ int orc_insert_batched(orc_graph* g, const double* u, uint64_t first, uint64_t n
         if (alloc_upper(g, q, l) || insert_layers(g, q, l, 1)) rc = -1;
     }
     /* 3. layer 0 of the new elements of level 0 */
-    if (rc == 0) rc = layer0_batches(g, Z, nz, first + nu, batch);
+    if (rc == 0) rc = layer0_batches(g, Z, nz, first + nu, batch, NULL, 0);
     free(U); free(Z); free(lv);
     return rc;
 }

@@ -101,11 +101,20 @@ int orc_build(orc_graph* g, const double* u);
  *     11's forward half), in selection order;
  *  3. each element e selected by batch elements takes them into its list,
  *     in ascending id: appended when they fit within Mmax0, otherwise the list
- *     becomes SELECT-NEIGHBORS(e, old members + new ones, Mmax0) over the 256
- *     candidates closest to e (lines 11-16).
+ *     becomes SELECT-NEIGHBORS(e, eConn, Mmax0) over all of eConn, the old
+ *     members and every new one (lines 11-16).
  * Elements of one batch do not see one another; batch = 1 is Alg. 1 applied
- * in the order seed, then the rest.  extendCandidates must be off. */
+ * in the order seed, then the rest.  The batch sizes are a free parameter of
+ * this form (the paper's parallel construction fixes none); the growing
+ * schedule keeps each batch at most 1/16 of the elements already present.
+ * extendCandidates must be off. */
 int orc_build_batched(orc_graph* g, const double* u, uint64_t n_first, uint32_t batch);
+
+/* orc_build_batched with explicit batch sizes: batch j holds sizes[j]
+ * elements (the last size repeats; every size clipped to what remains; a
+ * zero size is an error). */
+int orc_build_batched_sizes(orc_graph* g, const double* u, uint64_t n_first, const uint32_t* sizes,
+                            uint64_t n_sizes);
 
 /* Incremental insertion of elements first..first+n-1 (rows of the data, not
  * inserted yet) into a graph holding exactly elements 0..first-1, levels

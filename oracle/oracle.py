@@ -56,6 +56,7 @@ def lib():
                 "orc_insert": (i32, [vp, u32, i32]),
                 "orc_build": (i32, [vp, vp]),
                 "orc_build_batched": (i32, [vp, vp, u64, u32]),
+                "orc_build_batched_sizes": (i32, [vp, vp, u64, vp, u64]),
                 "orc_insert_batched": (i32, [vp, vp, u64, u64, u32]),
                 "orc_knn_search": (i32, [vp, vp, i32, i32, vp, vp, vp]),
                 "orc_search_layer": (i32, [vp, vp, vp, i32, i32, i32, vp, vp, vp]),
@@ -124,15 +125,22 @@ class Graph:
         return g
 
     @classmethod
-    def build_batched(cls, data, u, n_first: int = 4096, batch: int = 0, **kw) -> "Graph":
+    def build_batched(cls, data, u, n_first: int = 4096, batch: int = 0, batch_sizes=None, **kw) -> "Graph":
         """Alg. 1 with the layer-0 insertions in batches (orc_build_batched):
         the seed (level >= 1 or id < n_first) first, then the others in
-        batches that search the graph as it stood before the batch."""
+        batches that search the graph as it stood before the batch.  Batch
+        sizes: the list `batch_sizes` when given (orc_build_batched_sizes),
+        else `batch` elements each, else the growing schedule."""
         g = cls.new(data, **kw)
         u = np.ascontiguousarray(u, dtype=np.float64)
         if u.shape[0] != g._data.shape[0]:
             raise ValueError("one u per element")
-        if lib().orc_build_batched(g.h, _p(u), int(n_first), int(batch)) != 0:
+        if batch_sizes is not None:
+            sz = np.ascontiguousarray(batch_sizes, dtype=np.uint32)
+            rc = lib().orc_build_batched_sizes(g.h, _p(u), int(n_first), _p(sz), int(sz.shape[0]))
+        else:
+            rc = lib().orc_build_batched(g.h, _p(u), int(n_first), int(batch))
+        if rc != 0:
             raise RuntimeError("orc_build_batched failed")
         return g
 

@@ -177,3 +177,48 @@ def test_incremental_rejects_bad_ranges():
         g.insert_batched(300, np.ones(300))  # beyond the rows
     g.insert_batched(300, u[300:500])
     assert g.N == 500
+
+
+def test_explicit_schedule_is_the_default_schedule():
+    """The batch sizes are a free parameter of the batch form; the default is
+    the growing schedule max(64, inserted / 16) (at most 32,768, at most what
+    remains).  Passing that schedule explicitly, computed here, gives the
+    same graph byte for byte, and a different schedule gives another graph."""
+    p = synth.params("tiny")
+    N, n_first = 6000, 500
+    X = synth.base("tiny", N)
+    u = synth.level_uniforms("tiny", N)
+    seed, rest = _order(_levels(u, p["M"]), n_first)
+    sizes = _schedule(len(seed), len(rest))
+    g0 = O.Graph.build_batched(X, u, n_first=n_first, **p).to_blob()
+    g1 = O.Graph.build_batched(X, u, n_first=n_first, batch_sizes=sizes, **p).to_blob()
+    assert g0 == g1
+    g2 = O.Graph.build_batched(X, u, n_first=n_first, batch_sizes=[sizes[0] * 2], **p).to_blob()
+    assert g2 != g0
+
+
+def test_shrink_takes_all_of_econn_when_a_list_gets_over_256_new_links():
+    """Alg. 1 lines 13-15 shrink over the whole of eConn.  The hub input sends
+    all 301 ray points of one batch to the hub: its list then holds, by
+    Alg. 4 worked by hand, the t = 1 point of rays 0..9 (each closer to the
+    hub, at 1, than to any other accepted point, at 2; every further point of
+    a ray is closer to that ray's t = 1 point than to the hub; every filler f
+    is closer to the t = 1 point of ray k than to the hub, since f_k - 100 >=
+    80) and the t = 40 point of ray 10 (1,600 from the hub against 1,601 to
+    each t = 1 point).  That point is the 301st candidate by distance: a
+    shrink over the 256 closest would miss it."""
+    import _hub
+    X, u = _hub.hub_input()
+    n = X.shape[0]
+    seed, rest = _order(_levels(u, _hub.PARAMS["M"]), _hub.N_SEED)
+    sizes = _schedule(len(seed), len(rest))
+    assert sizes == list(_hub.FILL_BATCHES) + [_hub.RAYS]
+    g = O.Graph.build_batched(X, u, n_first=_hub.N_SEED, **_hub.PARAMS)
+    first, near, far = _hub.ray_ids(n)
+    # every ray point of the last batch linked to the hub: 301 > 256 new links
+    assert all(0 in g.neighbors(i, 0) for i in range(first, n))
+    assert g.neighbors(0, 0) == near + [far]
+    # the far point's rank among the hub's candidates (all 301 ray points
+    # precede every filler: squared distances <= 1,600 against >= 102,400)
+    d2 = ((X[first:] - X[0]) ** 2).sum(1)
+    assert int(np.sum(d2 < d2[-1])) == _hub.RAYS - 1 > 256
