@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define HNSW_ABI_VERSION 1
+#define HNSW_ABI_VERSION 2
 #define HNSW_NO_ID 0xFFFFFFFFu
 
 typedef enum {
@@ -102,8 +102,8 @@ void hnsw_free_blob(void* blob);
  * it stood before the batch (SEARCH-LAYER with ef = efConstruction on layer
  * 0 after the upper-layer descent), links to the M neighbours its selection
  * keeps, and each element it links to takes it into its list, shrinking the
- * list with the same selection when it exceeds Mmax0 (over the 256 closest
- * candidates when there are more).  Elements of one batch do not search one
+ * list with the same selection over all its old and new members when it
+ * exceeds Mmax0 (Alg. 1 lines 13-15).  Elements of one batch do not search one
  * another, so the graph differs from sequential insertion; it has the same
  * structure and format as hnsw_build's (validated the same way on upload).
  * data and level_u are host memory as for hnsw_build; device memory of about
@@ -208,7 +208,9 @@ typedef struct {
     int32_t max_level;
     uint32_t enter_point;
     uint64_t n_upper_rows;
-    uint64_t device_bytes;
+    uint64_t device_bytes;   /* the index arrays */
+    uint64_t staging_bytes;  /* device buffers hnsw_search_ex holds for calls with host
+                              * pointers (one per stream); hnsw_search_noalloc never adds any */
 } hnsw_index_info;
 
 /* Copies the index's shape and sizes into *out (host).  Never touches the
@@ -359,6 +361,28 @@ hnsw_status hnsw_stop_train(const float* x, const float* y, int64_t n, const hns
  * Errors: as hnsw_search, plus HNSW_EINVAL for the size limit. */
 hnsw_status hnsw_search_noalloc(hnsw_index* index, const float* queries, int64_t n, int32_t k, int32_t ef,
                                 uint32_t* out_ids, float* out_dists, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Data-sharded search (Section 6 discusses distributing HNSW by partitioning */
+/* the data)                                                                  */
+/* ------------------------------------------------------------------------ */
+/* The exchange step of data-sharded search.  Shard s holds its own graph over
+ * the elements with global ids id_base[s] .. id_base[s] + N_s - 1 (disjoint
+ * ranges) and has answered n queries with its own k nearest, in local ids:
+ * shard_ids[s][q][j], shard_dists[s][q][j] ([n_shards][n][k] row-major,
+ * each list sorted ascending by (distance, local id) and padded with
+ * HNSW_NO_ID, as hnsw_search writes them).  Writes, per query, the k smallest
+ * keys (distance, global id) over all shards' lists -- the answer of the
+ * whole data set's shards taken together -- to out_ids[n][k] (global ids) and
+ * out_dists[n][k], padded with HNSW_NO_ID / +inf when the shards hold fewer
+ * than k.  id_base is host memory (n_shards values; every global id must be
+ * below 2^32 - 1); the four buffers are device memory of the current device;
+ * asynchronous on `stream`.
+ * Errors: HNSW_EINVAL (n_shards outside [1, 32], n < 0, k outside [1, 1024],
+ * null or non-device buffers), HNSW_ECUDA. */
+hnsw_status hnsw_merge_topk(const uint32_t* shard_ids, const float* shard_dists, int32_t n_shards,
+                            const uint32_t* id_base, int64_t n, int32_t k, uint32_t* out_ids, float* out_dists,
+                            void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching over resident indexes (an addition; the      */

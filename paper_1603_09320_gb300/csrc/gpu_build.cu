@@ -49,8 +49,9 @@ using namespace hnswgb;
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxDW = 8;      // coordinates per lane: d <= 256
-constexpr int kKeep = 256;     // closest candidates kept for a shrink
+constexpr int kKeep = 256;     // shrink candidates examined per chunk (ascending key order)
 constexpr int kKeyBuf = 512;   // candidate keys sorted at once in a shrink
+constexpr int kMaxOld = 64;    // members of a layer-0 list (Mmax0 <= 64)
 constexpr int kWarps = 4;      // most warps per block of the selection kernels
 
 __device__ __forceinline__ uint32_t f2ord(float f) {
@@ -66,35 +67,41 @@ struct WarpSmem {
     float* Rv;       // [cap][dp] vectors of the accepted elements
     uint32_t* Rid;   // [cap]
     float* Rd;       // [cap] their distances to the base element
-    uint8_t* flag;   // [ncap] 1 = discarded (for keepPrunedConnections)
+    uint32_t* Did;   // [cap] the first discarded candidates, in order (keepPrunedConnections)
+    float* Dd;       // [cap]
     uint64_t* keys;  // [kKeyBuf] shrink candidates, (ordered distance, id)
+    uint64_t* okeys; // [kMaxOld] keys of a list's current members
     uint32_t* cid;   // [kKeep] sorted shrink candidates
     float* cd;       // [kKeep]
 };
 
-__host__ __device__ inline size_t warp_smem_bytes(int cap, uint32_t dp, int ncap) {
-    size_t b = size_t(cap) * dp * 4 + size_t(cap) * 8;
-    b += (size_t(ncap) + 15) & ~size_t(15);
-    b += size_t(kKeyBuf) * 8 + size_t(kKeep) * 8;
+__host__ __device__ inline size_t warp_smem_bytes(int cap, uint32_t dp) {
+    size_t b = size_t(kKeyBuf) * 8 + size_t(kMaxOld) * 8;
+    b += size_t(cap) * dp * 4 + size_t(cap) * 16;
+    b += size_t(kKeep) * 8;
     return (b + 15) & ~size_t(15);
 }
 
-__device__ inline WarpSmem carve(uint8_t* base, int cap, uint32_t dp, int ncap) {
+__device__ inline WarpSmem carve(uint8_t* base, int cap, uint32_t dp) {
     WarpSmem w;
     uint8_t* p = base;
     w.keys = reinterpret_cast<uint64_t*>(p);
     p += size_t(kKeyBuf) * 8;
+    w.okeys = reinterpret_cast<uint64_t*>(p);
+    p += size_t(kMaxOld) * 8;
     w.Rv = reinterpret_cast<float*>(p);
     p += size_t(cap) * dp * 4;
     w.Rid = reinterpret_cast<uint32_t*>(p);
     p += size_t(cap) * 4;
     w.Rd = reinterpret_cast<float*>(p);
     p += size_t(cap) * 4;
+    w.Did = reinterpret_cast<uint32_t*>(p);
+    p += size_t(cap) * 4;
+    w.Dd = reinterpret_cast<float*>(p);
+    p += size_t(cap) * 4;
     w.cid = reinterpret_cast<uint32_t*>(p);
     p += size_t(kKeep) * 4;
     w.cd = reinterpret_cast<float*>(p);
-    p += size_t(kKeep) * 4;
-    w.flag = p;
     return w;
 }
 
@@ -131,16 +138,17 @@ __device__ __forceinline__ float dist_sm(const float (&x)[kMaxDW], const float* 
     return metric == HNSW_L2SQ ? s : 1.0f - s;
 }
 
-// SELECT-NEIGHBORS over candidates (cid[i], cd[i]), i < nc, sorted by
-// (distance to the base, id), into R (w.Rid/Rd/Rv), at most cap entries.
+// SELECT-NEIGHBORS, resumable: takes the candidates (cid[i], cd[i]), i < nc,
+// sorted by (distance to the base, id) and following every candidate of
+// earlier calls, into R (w.Rid/Rd/Rv; nr entries so far), at most cap.
 // heuristic: Alg. 4 lines 9-14 without extendCandidates (a candidate is
 // accepted when it is closer to the base than to every element accepted
-// before it, strictly), then lines 15-17 with keep_pruned; otherwise Alg. 3
-// (the cap nearest).  Returns |R|.
-__device__ int select_links(const float* rows, uint32_t stride, uint32_t d, uint32_t dp, int metric,
+// before it, strictly); the discarded ones are recorded in order (nd so far,
+// the first cap of them: lines 15-17 never take more).  Otherwise Alg. 3
+// (the cap nearest).
+__device__ void select_more(const float* rows, uint32_t stride, uint32_t d, uint32_t dp, int metric,
                             const uint32_t* cid, const float* cd, int nc, int cap, bool heuristic,
-                            bool keep_pruned, const WarpSmem& w, int lane) {
-    int nr = 0;
+                            const WarpSmem& w, int& nr, int& nd, int lane) {
     for (int i = 0; i < nc && nr < cap; ++i) {
         const uint32_t e = cid[i];
         const float de = cd[i];
@@ -154,7 +162,13 @@ __device__ int select_links(const float* rows, uint32_t stride, uint32_t d, uint
                     break;
                 }
         }
-        if (lane == 0) w.flag[i] = good ? 0 : 1;
+        if (!good) {
+            if (nd < cap && lane == 0) {
+                w.Did[nd] = e;
+                w.Dd[nd] = de;
+            }
+            nd += nd < cap;
+        }
         if (good) {
             if (heuristic) {
 #pragma unroll
@@ -171,17 +185,29 @@ __device__ int select_links(const float* rows, uint32_t stride, uint32_t d, uint
         }
         __syncwarp();
     }
-    if (heuristic && keep_pruned)
-        for (int i = 0; i < nc && nr < cap; ++i) {
-            if (w.flag[i]) {
-                if (lane == 0) {
-                    w.Rid[nr] = cid[i];
-                    w.Rd[nr] = cd[i];
-                }
-                ++nr;
-            }
+}
+
+// Alg. 4 lines 15-17 (keepPrunedConnections): the nearest discarded
+// candidates fill R up to cap.
+__device__ void append_pruned(const WarpSmem& w, int cap, int& nr, int nd, int lane) {
+    for (int i = 0; i < nd && nr < cap; ++i) {
+        if (lane == 0) {
+            w.Rid[nr] = w.Did[i];
+            w.Rd[nr] = w.Dd[i];
         }
+        ++nr;
+    }
     __syncwarp();
+}
+
+// SELECT-NEIGHBORS over one sorted candidate list; returns |R|.
+__device__ int select_links(const float* rows, uint32_t stride, uint32_t d, uint32_t dp, int metric,
+                            const uint32_t* cid, const float* cd, int nc, int cap, bool heuristic,
+                            bool keep_pruned, const WarpSmem& w, int lane) {
+    int nr = 0, nd = 0;
+    select_more(rows, stride, d, dp, metric, cid, cd, nc, cap, heuristic, w, nr, nd, lane);
+    __syncwarp();
+    if (heuristic && keep_pruned) append_pruned(w, cap, nr, nd, lane);
     return nr;
 }
 
@@ -206,7 +232,7 @@ __global__ void __launch_bounds__(kWarps * 32) select_forward(
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t b = blockIdx.x * nw + wib;
     if (b >= B) return;
-    const WarpSmem w = carve(smem + wib * warp_smem_bytes(M, dp, efc), M, dp, efc);
+    const WarpSmem w = carve(smem + wib * warp_smem_bytes(M, dp), M, dp);
     const uint32_t q = bids[b];
     const uint32_t* cid = res_id + uint64_t(b) * efc;
     const float* cd = res_d + uint64_t(b) * efc;
@@ -258,10 +284,16 @@ __device__ void sort_keys(uint64_t* a, int n, int lane) {
         }
 }
 
+__device__ __forceinline__ unsigned lanes_below(int lane) { return (1u << lane) - 1u; }
+
 // One warp per target element e (a segment of the sorted pairs): the new
 // elements linking to e join neighbourhood(e); when the list then exceeds
-// Mmax0 it is shrunk with SELECT-NEIGHBORS over the old and new members (the
-// kKeep closest to e when there are more).
+// Mmax0 it becomes SELECT-NEIGHBORS(e, eConn, Mmax0) over all of eConn, the
+// current members and the new ones (Alg. 1 lines 11-16).  Alg. 4 takes eConn
+// in ascending (distance, id) order and stops once Mmax0 are accepted; here
+// that order is walked in chunks of kKeep: each chunk is the kKeep smallest
+// keys above the previous chunk's last one (keys are distinct: ids are),
+// found by one pass over the candidates that sorts kKeyBuf keys at a time.
 __global__ void __launch_bounds__(kWarps * 32) link_reverse(
     const float* __restrict__ rows, uint32_t stride, uint32_t d, uint32_t dp, int metric,
     const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx, uint32_t npairs,
@@ -270,7 +302,7 @@ __global__ void __launch_bounds__(kWarps * 32) link_reverse(
     int keep_pruned) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const WarpSmem w = carve(smem + wib * warp_smem_bytes(Mmax0, dp, kKeep), Mmax0, dp, kKeep);
+    const WarpSmem w = carve(smem + wib * warp_smem_bytes(Mmax0, dp), Mmax0, dp);
     const uint32_t nsegs = *nseg;
     for (uint32_t s = blockIdx.x * nw + wib; s < nsegs; s += gridDim.x * nw) {
         const uint32_t i0 = seg[s];
@@ -288,11 +320,9 @@ __global__ void __launch_bounds__(kWarps * 32) link_reverse(
             __syncwarp();
             continue;
         }
-        // candidates: the current members (distance to e recomputed) and the
-        // new ones, keeping the kKeep closest by (distance, id)
+        // keys of the current members (their distances to e recomputed)
         float x[kMaxDW];
         load_vec(rows, stride, d, e, x, lane);
-        int nk = 0;
         for (int j = 0; j < n0; ++j) {
             const uint32_t c = row[j];
             float y[kMaxDW];
@@ -312,35 +342,58 @@ __global__ void __launch_bounds__(kWarps * 32) link_reverse(
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(kFull, sacc, o);
             const float dc = metric == HNSW_L2SQ ? sacc : 1.0f - sacc;
-            if (lane == 0) w.keys[nk] = (uint64_t(f2ord(dc)) << 32) | c;
-            ++nk;
+            if (lane == 0) w.okeys[j] = (uint64_t(f2ord(dc)) << 32) | c;
         }
-        uint32_t t = 0;
+        __syncwarp();
+        const int total = n0 + nin;
+        int nr = 0, nd = 0, seen = 0;
+        uint64_t last = 0;  // keys of the next chunk are above it (all keys in the first chunk)
+        bool first = true;
         for (;;) {
-            // fill the key buffer from the incoming pairs
-            const int room = kKeyBuf - nk;
-            const int take = min(room, int(uint32_t(nin) - t));
-            for (int u = lane; u < take; u += 32) {
-                const uint32_t pi = sidx[i0 + t + u];
-                w.keys[nk + u] = (uint64_t(f2ord(pdist[pi])) << 32) | pval[pi];
+            // the kKeep smallest candidate keys above `last`
+            int nk = 0;
+            for (int b0 = 0; b0 < total; b0 += 32) {
+                const int j = b0 + lane;
+                uint64_t k = ~0ull;
+                if (j < n0) {
+                    k = w.okeys[j];
+                } else if (j < total) {
+                    const uint32_t pi = sidx[i0 + uint32_t(j - n0)];
+                    k = (uint64_t(f2ord(pdist[pi])) << 32) | pval[pi];
+                }
+                const bool ok = j < total && (first || k > last);
+                const unsigned m = __ballot_sync(kFull, ok);
+                if (ok) w.keys[nk + __popc(m & lanes_below(lane))] = k;
+                nk += __popc(m);
+                if (nk > kKeyBuf - 32) {  // full: keep the kKeep smallest
+                    for (int u = nk + lane; u < kKeyBuf; u += 32) w.keys[u] = ~0ull;
+                    __syncwarp();
+                    sort_keys(w.keys, kKeyBuf, lane);
+                    nk = kKeep;
+                }
+                __syncwarp();
             }
-            nk += take;
-            t += uint32_t(take);
             int n2 = 32;
             while (n2 < nk) n2 <<= 1;
             for (int u = nk + lane; u < n2; u += 32) w.keys[u] = ~0ull;
             __syncwarp();
             sort_keys(w.keys, n2, lane);
             nk = min(nk, kKeep);
-            if (t >= uint32_t(nin)) break;
+            if (nk == 0) break;
+            for (int u = lane; u < nk; u += 32) {
+                w.cid[u] = uint32_t(w.keys[u] & 0xffffffffu);
+                w.cd[u] = ord2f(uint32_t(w.keys[u] >> 32));
+            }
+            __syncwarp();
+            select_more(rows, stride, d, dp, metric, w.cid, w.cd, nk, Mmax0, heuristic != 0, w, nr, nd, lane);
+            __syncwarp();
+            seen += nk;
+            if (nr >= Mmax0 || seen >= total) break;
+            last = w.keys[nk - 1];
+            first = false;
+            __syncwarp();
         }
-        for (int u = lane; u < nk; u += 32) {
-            w.cid[u] = uint32_t(w.keys[u] & 0xffffffffu);
-            w.cd[u] = ord2f(uint32_t(w.keys[u] >> 32));
-        }
-        __syncwarp();
-        const int nr = select_links(rows, stride, d, dp, metric, w.cid, w.cd, nk, Mmax0, heuristic != 0,
-                                    keep_pruned != 0, w, lane);
+        if (heuristic && keep_pruned) append_pruned(w, Mmax0, nr, nd, lane);
         for (int j = lane; j < Mmax0; j += 32) row[j] = j < nr ? w.Rid[j] : kNone;
         __syncwarp();
     }
@@ -415,13 +468,17 @@ hnsw_status insert_layer0(hnsw_index* ix, const DevIndex& view, const std::vecto
         while (nw > 1 && size_t(nw) * per_warp > 227 * 1024) --nw;
         return nw;
     };
-    const int fw_w = warps_for(warp_smem_bytes(M, dp, efc)), rv_w = warps_for(warp_smem_bytes(Mmax0, dp, kKeep));
-    const size_t fw_smem = size_t(fw_w) * warp_smem_bytes(M, dp, efc);
-    const size_t rv_smem = size_t(rv_w) * warp_smem_bytes(Mmax0, dp, kKeep);
+    const int fw_w = warps_for(warp_smem_bytes(M, dp)), rv_w = warps_for(warp_smem_bytes(Mmax0, dp));
+    const size_t fw_smem = size_t(fw_w) * warp_smem_bytes(M, dp);
+    const size_t rv_smem = size_t(rv_w) * warp_smem_bytes(Mmax0, dp);
     if (fw_smem > 227 * 1024 || rv_smem > 227 * 1024)
         return fail(HNSW_EINVAL, "layer-0 insertion: dimension too large for the selection kernels");
-    cudaFuncSetAttribute(select_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fw_smem));
-    cudaFuncSetAttribute(link_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rv_smem));
+    {
+        hnsw_status r = raise_smem_limit(reinterpret_cast<const void*>(select_forward), fw_smem, "layer-0 insertion");
+        if (r == HNSW_OK)
+            r = raise_smem_limit(reinterpret_cast<const void*>(link_reverse), rv_smem, "layer-0 insertion");
+        if (r != HNSW_OK) return r;
+    }
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -692,9 +749,8 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
     const DevIndex& V = a.v;
     const float* rows = reinterpret_cast<const float*>(V.vec);
     const uint32_t d = V.d, stride = V.row_chunks * 4, dp = V.row_chunks * 4;
-    const int ncap = a.efc > kKeep ? a.efc : kKeep;
-    const WarpSmem w = carve(smem, a.Mmax, dp, ncap);
-    uint8_t* p = smem + warp_smem_bytes(a.Mmax, dp, ncap);
+    const WarpSmem w = carve(smem, a.Mmax, dp);
+    uint8_t* p = smem + warp_smem_bytes(a.Mmax, dp);
     float* qs = reinterpret_cast<float*>(p);  // [dp] the element being inserted
     p += size_t(dp) * 4;
     float* rs = reinterpret_cast<float*>(p);  // [dp] a reverse-link target
@@ -907,8 +963,7 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
 }
 
 size_t upper_smem_bytes(int Mmax, uint32_t dp, int efc) {
-    const int ncap = efc > kKeep ? efc : kKeep;
-    return warp_smem_bytes(Mmax, dp, ncap) + size_t(dp) * 8 + size_t(wcap_of(efc)) * 8 + size_t(efc) * 8 +
+    return warp_smem_bytes(Mmax, dp) + size_t(dp) * 8 + size_t(wcap_of(efc)) * 8 + size_t(efc) * 8 +
            size_t(efc) * 8 + 64 * 4 + 32 * 4 + size_t(wcap_of(efc)) * 8;
 }
 
@@ -1121,7 +1176,10 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
         ua.state = static_cast<int*>(state.p);
         const size_t sm = upper_smem_bytes(Mmax, V.row_chunks * 4, efc);
         if (sm > 227 * 1024) return ins_fail(HNSW_EINVAL, "dimension too large for the upper-layer kernel");
-        step(cudaFuncSetAttribute(insert_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+        {
+            const hnsw_status r = raise_smem_limit(reinterpret_cast<const void*>(insert_upper), sm, "hnsw_insert");
+            if (r != HNSW_OK) return r;
+        }
         if (e == cudaSuccess) {
             insert_upper<<<1, 32, sm, s>>>(ua);
             e = cudaGetLastError();

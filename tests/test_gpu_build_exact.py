@@ -59,3 +59,29 @@ def test_gpu_insert_equals_batched_oracle():
         g, o = O.Graph.from_blob(gb), O.Graph.from_blob(ob)
         diff = [i for i in range(N) if g.neighbors(i, 0) != o.neighbors(i, 0)]
         raise AssertionError(f"{len(diff)} layer-0 lists differ, first {diff[:10]}")
+
+
+@pytest.mark.parametrize("keep", [False, True])
+def test_gpu_build_shrinks_over_all_of_econn(keep):
+    """A batch that sends 301 new links to one list (and to a few filler
+    lists): the GPU's reverse-link shrink walks the whole of eConn, as the
+    oracle's batch form does (Alg. 1 lines 13-15), byte for byte."""
+    import torch
+    assert torch.cuda.is_available()
+    import _hub
+    from oracle import oracle as O
+    from paper_1603_09320_gb300 import build, hnsw as H
+    build.build()
+    X, u = _hub.hub_input()
+    P = _hub.PARAMS
+    blob = H.build_graph_gpu(X, u, M=P["M"], Mmax=P["Mmax"], Mmax0=P["Mmax0"], ef_construction=P["efC"],
+                             heuristic=True, keep_pruned=keep, n_threads=1)
+    ob = O.Graph.build_batched(X, u, n_first=_hub.N_SEED, keep_pruned=keep, **P).to_blob()
+    g = O.Graph.from_blob(blob)
+    first, near, far = _hub.ray_ids(X.shape[0])
+    if not keep:
+        assert g.neighbors(0, 0) == near + [far]
+    if blob != ob:
+        o = O.Graph.from_blob(ob)
+        diff = [i for i in range(X.shape[0]) if g.neighbors(i, 0) != o.neighbors(i, 0)]
+        raise AssertionError(f"{len(diff)} layer-0 lists differ, first {diff[:10]}")
