@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -251,12 +253,37 @@ extern "C" hnsw_status hnsw_free_index(hnsw_index* ix) {
 extern "C" hnsw_status hnsw_get_index_info(const hnsw_index* ix, hnsw_index_info* out) {
     if (!ix || !out) return fail(HNSW_EINVAL, "hnsw_get_index_info: null pointer");
     // an insertion publishes N, top level, enter point and rows under dev_mu
-    std::lock_guard<std::mutex> lk(const_cast<hnsw_index*>(ix)->dev_mu);
-    *out = ix->info;
+    hnsw_index* m = const_cast<hnsw_index*>(ix);
+    {
+        std::lock_guard<std::mutex> lk(m->dev_mu);
+        *out = ix->info;
+    }
+    uint64_t sb = 0;
+    {
+        std::lock_guard<std::mutex> lk(m->stage_mu);
+        for (const auto& st : m->stages) sb += st.bytes;
+    }
+    out->staging_bytes = sb;
     return HNSW_OK;
 }
 
 namespace hnswgb {
+
+hnsw_status raise_smem_limit(const void* fn, size_t bytes, const char* who) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string(who) + ": " + cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[{dev, fn}];
+    if (cur >= bytes) return HNSW_OK;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e != cudaSuccess)
+        return fail(HNSW_ECUDA, std::string(who) + ": shared memory attribute: " + cudaGetErrorString(e));
+    cur = bytes;
+    return HNSW_OK;
+}
 
 hnsw_status store_rows(hnsw_index* ix, const float* rows32, uint64_t first, uint64_t n, cudaStream_t s) {
     if (n == 0) return HNSW_OK;

@@ -119,4 +119,9 @@ hnsw_status upload_index(const void* graph_blob, uint64_t blob_bytes, hnsw_dtype
 // Writes stored rows [first, first + n) (and the fp32 copy when kept) from
 // fp32 rows in device memory, d_pad32 floats apart; asynchronous on s.
 hnsw_status store_rows(hnsw_index* ix, const float* rows32, uint64_t first, uint64_t n, cudaStream_t s);
+
+// Raises kernel `fn`'s dynamic shared-memory limit on the current device to
+// at least `bytes`.  The limit is per device and is never lowered: a launch
+// issued by another thread after it raised the limit may still rely on it.
+hnsw_status raise_smem_limit(const void* fn, size_t bytes, const char* who);
 }  // namespace hnswgb

@@ -990,8 +990,6 @@ int ceil_log2(uint64_t x) {
     return r;
 }
 
-std::mutex g_attr_mu;
-
 }  // namespace
 
 int auto_visited_log2(int efp) {
@@ -1060,9 +1058,8 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     {
-        std::lock_guard<std::mutex> lk(g_attr_mu);
-        cudaError_t e = cudaFuncSetAttribute(kc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("search: smem attribute: ") + cudaGetErrorString(e));
+        const hnsw_status st = raise_smem_limit(reinterpret_cast<const void*>(kc.fn), smem, "search");
+        if (st != HNSW_OK) return st;
     }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc.fn, warps * 32, smem);
     if (per_sm < 1) per_sm = 1;
@@ -1269,10 +1266,11 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
         r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 1, keys, cnt, nullptr, nullptr,
                                nullptr, &snap);
         if (r == HNSW_OK) {
-            static bool attr = false;
-            if (!attr) {
-                cudaFuncSetAttribute(order_by_descent, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortChunk * 8);
-                attr = true;
+            r = raise_smem_limit(reinterpret_cast<const void*>(order_by_descent), size_t(kSortChunk) * 8,
+                                 "hnsw_search: order");
+            if (r != HNSW_OK) {
+                cudaFreeAsync(scr, s);
+                return r;
             }
             const unsigned chunks = unsigned((uint64_t(n) + kSortChunk - 1) / kSortChunk);
             order_by_descent<<<chunks, 1024, kSortChunk * 8, s>>>(keys, uint32_t(n), ord);
@@ -1286,9 +1284,10 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
         if (r != HNSW_OK) return r;
     }
     if (!di || !dd || !ds) {
-        if (!di) cudaMemcpyAsync(out_ids, ids, ob, cudaMemcpyDeviceToHost, s);
-        if (!dd) cudaMemcpyAsync(out_dists, dists, ob, cudaMemcpyDeviceToHost, s);
-        if (!ds) cudaMemcpyAsync(stats, st, sb, cudaMemcpyDeviceToHost, s);
+        if ((!di && (e = cudaMemcpyAsync(out_ids, ids, ob, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+            (!dd && (e = cudaMemcpyAsync(out_dists, dists, ob, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+            (!ds && (e = cudaMemcpyAsync(stats, st, sb, cudaMemcpyDeviceToHost, s)) != cudaSuccess))
+            return fail(HNSW_ECUDA, std::string("hnsw_search: D2H: ") + cudaGetErrorString(e));
     }
     if (!dq || !di || !dd || !ds) {
         e = cudaStreamSynchronize(s);

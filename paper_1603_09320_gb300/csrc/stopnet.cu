@@ -261,13 +261,7 @@ size_t smem_bytes() { return sizeof(TrainSmem); }
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
 hnsw_status set_smem() {
-    static bool done = false;
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(stop_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes()));
-        if (e != cudaSuccess) return cuda_err(e, "stop network: shared memory attribute");
-        done = true;
-    }
-    return HNSW_OK;
+    return raise_smem_limit(reinterpret_cast<const void*>(stop_fwd_bwd), smem_bytes(), "stop network");
 }
 
 }  // namespace
