@@ -130,8 +130,10 @@ extern "C" hnsw_status hnsw_search_noalloc(hnsw_index* ix, const float* queries,
     prm.stop_threshold = 2.0f;
     st = hnswgb::launch_search(ix, prm, q, uint32_t(n), ids, dists, nullptr, s, work, nullptr);
     if (st != HNSW_OK) return st;
-    if (!di) cudaMemcpyAsync(out_ids, ids, ob, cudaMemcpyDeviceToHost, s);
-    if (!dd) cudaMemcpyAsync(out_dists, dists, ob, cudaMemcpyDeviceToHost, s);
+    if (!di && (e = cudaMemcpyAsync(out_ids, ids, ob, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return fail(HNSW_ECUDA, std::string("hnsw_search_noalloc: D2H ids: ") + cudaGetErrorString(e));
+    if (!dd && (e = cudaMemcpyAsync(out_dists, dists, ob, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return fail(HNSW_ECUDA, std::string("hnsw_search_noalloc: D2H distances: ") + cudaGetErrorString(e));
     if (!dq || !di || !dd) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search_noalloc: ") + cudaGetErrorString(e));

@@ -38,7 +38,8 @@ class IndexInfo(C.Structure):
     _fields_ = [("N", C.c_uint64), ("d", C.c_uint32), ("d_pad", C.c_uint32), ("row_bytes", C.c_uint32),
                 ("metric", C.c_int32), ("storage", C.c_int32), ("has_fp32", C.c_int32),
                 ("M", C.c_uint32), ("Mmax", C.c_uint32), ("Mmax0", C.c_uint32), ("max_level", C.c_int32),
-                ("enter_point", C.c_uint32), ("n_upper_rows", C.c_uint64), ("device_bytes", C.c_uint64)]
+                ("enter_point", C.c_uint32), ("n_upper_rows", C.c_uint64), ("device_bytes", C.c_uint64),
+                ("staging_bytes", C.c_uint64)]
 
 
 class SearchParams(C.Structure):
@@ -111,6 +112,7 @@ def lib():
             "hnsw_stop_grad": (i32, [vp, vp, i64, vp, vp, vp, vp, vp]),
             "hnsw_stop_train": (i32, [vp, vp, i64, C.POINTER(StopTrainParams), vp, vp, vp, vp, vp]),
             "hnsw_abi_version": (i32, []),
+            "hnsw_merge_topk": (i32, [vp, vp, i32, vp, i64, i32, vp, vp, vp]),
             "hnsw_server_create": (i32, [C.POINTER(ServerParams), C.POINTER(vp)]),
             "hnsw_server_add_index": (i32, [vp, vp, C.POINTER(i32)]),
             "hnsw_server_submit": (i32, [vp, C.POINTER(Request), C.POINTER(u64)]),
@@ -350,6 +352,26 @@ class Index:
         self.search_into(queries, k, ef, ids, ds, st, rerank=rerank, visited_log2=visited_log2,
                          stop_threshold=stop_threshold, stop_period=stop_period, schedule=schedule, stream=stream)
         return (ids, ds, st) if stats else (ids, ds)
+
+
+def merge_topk(shard_ids, shard_dists, id_base, k: int, stream=None):
+    """hnsw_merge_topk: per-shard results [S][n][k] (CUDA tensors, local ids)
+    -> the k smallest (distance, global id) over the shards, ([n][k] int32
+    ids viewed as uint32, [n][k] float32), on the tensors' device."""
+    import torch
+    S, n, kk = shard_ids.shape
+    if kk != k or tuple(shard_dists.shape) != (S, n, k):
+        raise ValueError("shard results must be [S][n][k]")
+    base = np.ascontiguousarray(id_base, dtype=np.uint32)
+    if base.shape != (S,):
+        raise ValueError("one id base per shard")
+    si = shard_ids.contiguous()
+    sd = shard_dists.contiguous()
+    oi = torch.empty((n, k), dtype=torch.int32, device=si.device)
+    od = torch.empty((n, k), dtype=torch.float32, device=si.device)
+    _check(lib().hnsw_merge_topk(si.data_ptr(), sd.data_ptr(), S, base.ctypes.data, n, k, oi.data_ptr(),
+                                 od.data_ptr(), _stream_ptr(stream)))
+    return oi, od
 
 
 def stop_grad(x, y, norm12, w_fp16):

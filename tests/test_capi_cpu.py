@@ -29,7 +29,7 @@ def test_exports_every_declared_symbol(H):
     L = H.lib()
     for n in names:
         assert hasattr(L, n), n
-    assert L.hnsw_abi_version() == 1
+    assert L.hnsw_abi_version() == 2
 
 
 def test_builder_one_thread_equals_oracle(H, oracle):

@@ -75,3 +75,43 @@ def test_noalloc_rejects_batches_beyond_the_scratch():
     assert st == 1  # HNSW_EINVAL
     assert b"scratch" in hnsw.lib().hnsw_last_error()
     ix.close()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """A fresh index searched only through hnsw_search_noalloc with host
+    buffers holds no staging buffer afterwards, and the device's free memory
+    is the same before and after two calls (the first call on this device,
+    which resolves the fixed array's address and may load the module, runs
+    beforehand on another index)."""
+    import torch
+    from oracle import oracle as O
+    from paper_1603_09320_gb300 import build, hnsw
+    build.build()
+    p = synth.params("tiny")
+    X = synth.base("tiny", 3000)
+    blob = O.Graph.build(X, synth.level_uniforms("tiny", 3000), **p).to_blob()
+    Q = np.ascontiguousarray(synth.queries("tiny", 500))
+    n, k, ef = Q.shape[0], 10, 32
+    f = _noalloc(hnsw)
+    warm = hnsw.Index(blob, "f32")
+    ids = np.zeros((n, k), np.uint32)
+    ds = np.zeros((n, k), np.float32)
+    assert f(warm.h, Q.ctypes.data, n, k, ef, ids.ctypes.data, ds.ctypes.data, None) == 0
+    ix = hnsw.Index(blob, "f32")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        assert f(ix.h, Q.ctypes.data, n, k, ef, ids.ctypes.data, ds.ctypes.data, None) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    info = hnsw.IndexInfo()
+    assert hnsw.lib().hnsw_get_index_info(ix.h, info) == 0
+    assert info.staging_bytes == 0
+    assert free1 == free0
+    # hnsw_search with host buffers on the same index does stage (the
+    # counter sees a staging buffer when there is one)
+    assert hnsw.lib().hnsw_search(ix.h, Q.ctypes.data, n, k, ef, ids.ctypes.data, ds.ctypes.data, None) == 0
+    assert hnsw.lib().hnsw_get_index_info(ix.h, info) == 0
+    assert info.staging_bytes > 0
+    ix.close()
+    warm.close()
