@@ -48,3 +48,54 @@ def _oracle_graph(blob):
         _cache.clear()
         _cache[key] = O.Graph.from_blob(blob)
     return _cache[key]
+
+
+# The angular (GloVe-shaped 1.2M x 100, cosine, M=16, efC=500) and clustered
+# low-d (10M x 8, M=12, Mmax0=24, efC=100) workloads at their full sizes, in
+# the bench's launch configuration (10,000 queries per launch), on graphs
+# built by hnsw_build_gpu.  Their coordinates are general floats, so the
+# bar is the tolerance of test_gpu_search: relative distance error <= 1e-5
+# (cosine: with the fp32 floor 0.12) and result-set overlap >= 0.999 on the
+# sampled queries, which the oracle answers one by one on the same graph.
+# With bf16 / f16 storage and the fp32 rerank the returned distances are the
+# exact fp32 distances of the returned ids, sorted.
+@pytest.mark.parametrize("name,N,cases", [
+    ("glove", 1_200_000, [("f32", False, 10, 96), ("f32", False, 10, 800), ("bf16", True, 10, 498)]),
+    ("lowd", 10_000_000, [("f32", False, 1, 10), ("f32", False, 10, 200), ("f16", True, 10, 32)]),
+])
+def test_fullsize_sampled_tolerance(name, N, cases):
+    import torch
+    from oracle import oracle as O
+    from paper_1603_09320_gb300 import build, hnsw
+    from test_gpu_search import COSINE_FLOOR, _tolerance_check
+    build.build()
+    p = synth.params(name)
+    X = synth.base(name, N)
+    u = synth.level_uniforms(name, N)
+    blob = hnsw.build_graph_gpu(X, u, metric=p["metric"], M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"],
+                                ef_construction=p["efC"])
+    del X
+    Q = synth.queries(name, 10_000)
+    q = torch.from_numpy(Q).cuda()
+    rng = np.random.default_rng(1)
+    sample = np.concatenate([[0, 9999], rng.choice(np.arange(1, 9999), size=38, replace=False)])
+    results = []
+    for storage, rerank, k, ef in cases:
+        ix = hnsw.Index(blob, storage, keep_fp32=rerank)
+        ids, ds = ix.search(q, k, ef, rerank=rerank)
+        torch.cuda.synchronize()
+        results.append((storage, rerank, k, ef, ids.cpu().numpy().view(np.uint32)[sample], ds.cpu().numpy()[sample]))
+        ix.close()
+    g = O.Graph.from_blob(blob)
+    floor = COSINE_FLOOR if p["metric"] == 1 else 0.0
+    for storage, rerank, k, ef, gi, gd in results:
+        if storage == "f32":
+            res = [g.knn_search(Q[i], k, ef) for i in sample]
+            oi = np.stack([r[0] for r in res])
+            od = np.stack([r[1] for r in res])
+            _tolerance_check(gi, gd, oi, od, d_floor=floor)
+        else:
+            ex = np.array([[g.dist(Q[i], int(j)) for j in gi[r]] for r, i in enumerate(sample)])
+            err = np.abs(gd.astype(np.float64) - ex) / np.maximum(np.abs(ex), max(floor, 1e-30))
+            assert err.max() <= 1e-5, err.max()
+            assert np.all(np.diff(gd, axis=1) >= 0)

@@ -129,12 +129,28 @@ def test_sift_shaped_bit_exact(H, storage, keep, rerank):
     np.testing.assert_array_equal(gd.astype(np.float64), od)
 
 
-def _tolerance_check(gi, gd, oi, od, overlap_min=0.999, rel=1e-5):
+# Cosine distances are 1 - <q, x> on unit vectors.  In the kernel's fp32 dot
+# product every term passes through at most 19 roundings (a lane chains at
+# most 16 fused multiply-adds for d <= 128, then three shuffle additions
+# combine the lanes of a team), so its absolute error is at most
+# gamma_19 sum|q_i x_i| <= 19u / (1 - 19u) (u = 2^-24; sum|q_i x_i| <= |q||x|
+# = 1), plus u for 1 - s: below 1.2e-6.  A relative bound of 1e-5 on d
+# therefore holds for d >= 0.12; below that the bound is 1e-5 * 0.12
+# absolute.  (Measured in an fp32 simulation on the glove-shaped data, whose
+# nearest distances are 0.09-0.3: absolute errors <= 1.4e-7.)
+COSINE_FLOOR = 0.12
+
+
+def _tolerance_check(gi, gd, oi, od, overlap_min=0.999, rel=1e-5, d_floor=0.0):
+    """Result-set overlap >= overlap_min, and |d_gpu - d_oracle| <=
+    rel * max(|d_oracle|, d_floor) wherever both return the same id at the
+    same rank."""
     ov = np.mean([len(set(gi[i]) & set(oi[i])) / gi.shape[1] for i in range(gi.shape[0])])
-    assert ov >= overlap_min, ov
     m = gi == oi
-    err = np.abs(gd[m].astype(np.float64) - od[m]) / np.maximum(np.abs(od[m]), 1e-30)
+    err = np.abs(gd[m].astype(np.float64) - od[m]) / np.maximum(np.abs(od[m]), max(d_floor, 1e-30))
+    assert ov >= overlap_min, f"overlap {ov}"
     assert err.max() <= rel, err.max()
+    return ov, float(err.max())
 
 
 def test_glove_cosine_tolerance(H):
@@ -142,7 +158,9 @@ def test_glove_cosine_tolerance(H):
     Q = synth.queries("glove", 500)
     gi, gd = gpu_search(H, blob, Q, 10, 64)
     oi, od, _ = oracle_batch(g, Q, 10, 64)
-    # cosine distances near 0 make relative error large: compare 1 - d (similarity)
+    # the distance itself, relative, with the fp32 floor derived above ...
+    _tolerance_check(gi, gd, oi, od, d_floor=COSINE_FLOOR)
+    # ... and the similarity 1 - d, relative
     _tolerance_check(gi, 1.0 - gd.astype(np.float64), oi, 1.0 - od)
 
 

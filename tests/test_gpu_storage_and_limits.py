@@ -4,9 +4,9 @@ other search tests).
 
 * Without rerank a quantised index returns the distances to its decoded rows
   (oracle/quant_oracle.py: round-to-nearest-even codes, fp8-e4m3 with the
-  row scale max|x| / 448): relative error <= 1e-5 for every returned id, and
-  the oracle's search of the same graph over those rows agrees (overlap
-  >= 0.995).
+  row scale max|x| / 448): relative error <= 1e-5 for every returned id (for
+  cosine with the floor 0.12 of the fp32 bound), and the oracle's search of
+  the same graph over those rows agrees (overlap >= 0.999).
 * At k = 1024 and ef' = 1024 (the kernel's limits) ids, distances and
   layer-0 expansion counts are bit-exact on integer data.
 """
@@ -15,7 +15,7 @@ import pytest
 
 from paper_1603_09320_gb300 import synth
 from _graphs import oracle_graph
-from test_gpu_search import _tolerance_check, gpu_search, oracle_batch
+from test_gpu_search import COSINE_FLOOR, _tolerance_check, gpu_search, oracle_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +55,7 @@ def test_quantised_distances_are_those_of_the_decoded_rows(H, storage, name):
     gi, gd = gpu_search(H, blob, Q, 10, 96, storage=storage)
     oi, od, _ = oracle_batch(h, Q, 10, 96)
     ex = np.array([[h.dist(Q[i], int(j)) for j in gi[i]] for i in range(len(Q))])
-    if name == "glove":  # cosine: compare the similarity 1 - d
-        gd, od, ex = 1.0 - gd.astype(np.float64), 1.0 - od, 1.0 - ex
-    np.testing.assert_allclose(gd, ex, rtol=1e-5, atol=0)
-    _tolerance_check(gi, gd, oi, od, overlap_min=0.995)
+    floor = COSINE_FLOOR if name == "glove" else 0.0
+    err = np.abs(gd.astype(np.float64) - ex) / np.maximum(np.abs(ex), max(floor, 1e-30))
+    assert err.max() <= 1e-5, err.max()
+    _tolerance_check(gi, gd, oi, od, d_floor=floor)
