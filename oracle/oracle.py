@@ -295,3 +295,26 @@ def brute_force(data, Q, K: int, metric: int = 0):
         lib().orc_brute_force(_p(data), N, d, metric, _p(Q[i]), K,
                               ids[i].ctypes.data_as(C.c_void_p), ds[i].ctypes.data_as(C.c_void_p))
     return ids, ds
+
+
+def merge_by_key(shard_ids, shard_dists, id_base, K: int):
+    """Data-sharded search's merge, by its definition: for each query the K
+    smallest keys (distance, global id) of the union of the shards' answers,
+    global id = id_base[s] + local id; NONE entries are absent; padded with
+    (NONE, +inf).  shard_ids / shard_dists are [S][n][k] arrays."""
+    shard_ids = np.asarray(shard_ids, dtype=np.uint64)
+    shard_dists = np.asarray(shard_dists, dtype=np.float64)
+    S, n, _ = shard_ids.shape
+    ids = np.full((n, K), NONE, dtype=np.uint32)
+    ds = np.full((n, K), np.inf, dtype=np.float64)
+    for q in range(n):
+        keys = []
+        for s in range(S):
+            for j in range(shard_ids.shape[2]):
+                if shard_ids[s, q, j] != NONE:
+                    keys.append((float(shard_dists[s, q, j]), int(id_base[s]) + int(shard_ids[s, q, j])))
+        keys.sort()
+        for j, (dd, ii) in enumerate(keys[:K]):
+            ids[q, j] = ii
+            ds[q, j] = dd
+    return ids, ds

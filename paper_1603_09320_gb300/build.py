@@ -24,7 +24,7 @@ CU_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-rel
             "-I", INCLUDE]
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", "/usr/local/cuda/include"]
 
-SOURCES = ["search.cu", "search_noalloc.cu", "index.cu", "stopnet.cu", "gpu_build.cu", "builder.cpp", "blob.cpp",
+SOURCES = ["search.cu", "search_noalloc.cu", "merge.cu", "index.cu", "stopnet.cu", "gpu_build.cu", "builder.cpp", "blob.cpp",
            "server.cpp"]
 HEADERS = ["common.hpp", "index.cuh", "stopnet.cuh"]
 
