@@ -64,7 +64,7 @@ typedef struct hnsw_index hnsw_index;
 /* Construction parameters (Alg. 1 inputs; Mmax0 from Section 4.1, where 2*M is
  * recommended).  mL is the level normalisation (1/ln M recommended). */
 typedef struct {
-    uint32_t M;                 /* links made per inserted element (Alg. 1 line 10) */
+    uint32_t M;                 /* links made per inserted element (Alg. 1) */
     uint32_t Mmax;              /* cap on links per element on layers >= 1 */
     uint32_t Mmax0;             /* cap on layer 0 */
     uint32_t ef_construction;   /* beam width of SEARCH-LAYER during insertion */
@@ -78,7 +78,7 @@ typedef struct {
 /* Builds the HNSW graph of `data` (fp32 row-major [N][d], host memory) by
  * concurrent insertion of elements 0..N-1 (Alg. 1; Section 4.1: parallel
  * construction with per-element locks and one lock for the enter point).
- * Element i gets level floor(-ln(level_u[i]) * mL) (Alg. 1 line 4); level_u
+ * Element i gets level floor(-ln(level_u[i]) * mL) (the level draw of Alg. 1); level_u
  * holds N host doubles in (0,1].  With n_threads = 1 elements are inserted in
  * id order, which is exactly Alg. 1 applied sequentially.
  * On success *out_blob receives a library-allocated graph blob in the
@@ -103,7 +103,7 @@ void hnsw_free_blob(void* blob);
  * 0 after the upper-layer descent), links to the M neighbours its selection
  * keeps, and each element it links to takes it into its list, shrinking the
  * list with the same selection over all its old and new members when it
- * exceeds Mmax0 (Alg. 1 lines 13-15).  Elements of one batch do not search one
+ * exceeds Mmax0 (Alg. 1's shrink).  Elements of one batch do not search one
  * another, so the graph differs from sequential insertion; it has the same
  * structure and format as hnsw_build's (validated the same way on upload).
  * data and level_u are host memory as for hnsw_build; device memory of about

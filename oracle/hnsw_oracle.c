@@ -181,7 +181,7 @@ void orc_free(orc_graph* g) {
     free(g);
 }
 
-/* Alg. 1, line 4: l <- floor(-ln(unif(0..1)) * mL), u supplied in (0,1]. */
+/* Alg. 1, the level draw: l <- floor(-ln(unif(0..1)) * mL), u supplied in (0,1]. */
 int orc_level_from_u(double u, double mL) { return (int)floor(-log(u) * mL); }
 
 /* ------------------------------------------------------------------------ */
@@ -206,7 +206,7 @@ static int search_layer_items_tr(const orc_graph* g, const float* q, const orc_i
     unsigned char* v = (unsigned char*)calloc(g->N > 0 ? g->N : 1, 1);
     orc_heap C, W;
     if (!v || !heap_init(&C, 64, 0) || !heap_init(&W, ef + 2, 1)) { free(v); return -1; }
-    /* lines 1-3: v <- ep, C <- ep, W <- ep */
+    /* start: v <- ep, C <- ep, W <- ep */
     for (int i = 0; i < n_ep; ++i) {
         if (v[ep[i].id]) continue;
         v[ep[i].id] = 1;
@@ -216,25 +216,25 @@ static int search_layer_items_tr(const orc_graph* g, const float* q, const orc_i
     uint64_t n_eval0 = 0, n_exp = 0, stale = 0;
     orc_item last_kth = { INFINITY, ORC_NONE };
     orc_item* sorted = tr ? (orc_item*)malloc(sizeof(orc_item) * (size_t)(ef + n_ep + 2)) : NULL;
-    /* line 4 */
+    /* while C is not empty */
     while (C.n > 0) {
-        orc_item c = heap_pop(&C);              /* line 5: nearest in C */
-        orc_item f = W.a[0];                    /* line 6: furthest in W */
-        if (key_less(f, c)) break;              /* lines 7-8: key(c) > key(f) */
+        orc_item c = heap_pop(&C);              /* extract the nearest of C */
+        orc_item f = W.a[0];                    /* the furthest of W */
+        if (key_less(f, c)) break;              /* stop when key(c) > key(f) */
         if (st) { if (lc == 0) st->n_hops0++; else st->n_hopsU++; }
         const uint32_t* nb = nbh(g, c.id, lc);
-        for (uint32_t j = 0; j < nb[0]; ++j) { /* line 9 */
+        for (uint32_t j = 0; j < nb[0]; ++j) { /* each neighbour e of c at layer lc */
             uint32_t e = nb[1 + j];
-            if (v[e]) continue;                 /* line 10 */
-            v[e] = 1;                           /* line 11 */
-            f = W.a[0];                         /* line 12 */
+            if (v[e]) continue;                 /* skip visited */
+            v[e] = 1;                           /* mark visited */
+            f = W.a[0];                         /* the furthest of W again */
             orc_item ei = { dist_vec(g, q, row(g, e)), e };
             if (st) st->n_dist++;
             n_eval0++;
-            if (key_less(ei, f) || W.n < ef) {  /* line 13 */
-                heap_push(&C, ei);              /* line 14 */
-                heap_push(&W, ei);              /* line 15 */
-                if (W.n > ef) heap_pop(&W);     /* lines 16-17 */
+            if (key_less(ei, f) || W.n < ef) {  /* admit e: closer than f, or W not full */
+                heap_push(&C, ei);              /* into C */
+                heap_push(&W, ei);              /* into W */
+                if (W.n > ef) heap_pop(&W);     /* drop the furthest when W exceeds ef */
             }
         }
         if (tr && sorted) {   /* state after this expansion */
@@ -340,9 +340,9 @@ static int select_heuristic_items(const orc_graph* g, const float* base, uint32_
     if (!R || !inW || !heap_init(&Wq, n + 4, 0) || !heap_init(&Wd, n + 4, 0)) {
         free(R); free(inW); return -1;
     }
-    /* line 2: W <- C */
+    /* the working queue W <- C */
     for (int i = 0; i < n; ++i) { heap_push(&Wq, C[i]); inW[C[i].id] = 1; }
-    /* lines 3-7: extend the candidates by their neighbourhoods at layer lc */
+    /* extendCandidates: add the candidates' neighbourhoods at layer lc */
     if (extend) {
         for (int i = 0; i < n; ++i) {
             const uint32_t* nb = nbh(g, C[i].id, lc);
@@ -355,7 +355,7 @@ static int select_heuristic_items(const orc_graph* g, const float* base, uint32_
             }
         }
     }
-    /* lines 9-14 */
+    /* accept e when it is closer to the base than to every element of R */
     while (Wq.n > 0 && nR < M) {
         orc_item e = heap_pop(&Wq);
         int good = 1;
@@ -366,7 +366,7 @@ static int select_heuristic_items(const orc_graph* g, const float* base, uint32_
         if (good) R[nR++] = e;
         else heap_push(&Wd, e);
     }
-    /* lines 15-17 */
+    /* keepPrunedConnections: refill R from the discarded, nearest first */
     if (keep)
         while (Wd.n > 0 && nR < M) R[nR++] = heap_pop(&Wd);
     for (int i = 0; i < nR; ++i) out[i] = R[i].id;
@@ -414,7 +414,7 @@ static int has_link(const uint32_t* list, uint32_t x) {
     return 0;
 }
 
-/* Alg. 1 lines 2-19 for element qid of level l (level and lists already
+/* Alg. 1 (everything after the level draw) for element qid of level l (level and lists already
  * set up), on layers lc >= lc_min only: lc_min = 0 is the whole insertion,
  * lc_min = 1 the upper layers of an element already linked on layer 0. */
 static int insert_layers(orc_graph* g, uint32_t qid, int l, int lc_min) {
@@ -426,24 +426,24 @@ static int insert_layers(orc_graph* g, uint32_t qid, int l, int lc_min) {
     uint32_t* sel = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(g->Mmax0 + 2 + cap_w));
     if (!W || !ep || !cand || !sel) { free(W); free(ep); free(cand); free(sel); return -1; }
 
-    /* lines 2-3 */
+    /* enter point and top level */
     int n_ep = 1;
     ep[0].id = g->ep;
     ep[0].d = dist_vec(g, q, row(g, g->ep));
     int L = g->maxlevel;
-    /* lines 5-7: greedy ef = 1 descent through layers L .. l+1 */
+    /* greedy ef = 1 descent through layers L .. l+1 */
     for (int lc = L; lc > l; --lc) {
         int n = search_layer_items(g, q, ep, n_ep, 1, lc, W, NULL);
         ep[0] = W[0];
         n_ep = 1;
         (void)n;
     }
-    /* lines 8-17 */
+    /* layers min(L, l) .. 0 */
     for (int lc = (L < l ? L : l); lc >= lc_min; --lc) {
-        int nW = search_layer_items(g, q, ep, n_ep, (int)g->efC, lc, W, NULL);  /* line 9 */
+        int nW = search_layer_items(g, q, ep, n_ep, (int)g->efC, lc, W, NULL);  /* SEARCH-LAYER with efConstruction */
         for (int i = 0; i < nW; ++i) cand[i] = W[i];
-        int nsel = select_items(g, q, qid, cand, nW, (int)g->M, lc, sel);         /* line 10 */
-        /* line 11: bidirectional connections */
+        int nsel = select_items(g, q, qid, cand, nW, (int)g->M, lc, sel);         /* SELECT-NEIGHBORS(q, W, M) */
+        /* bidirectional connections */
         uint32_t* ql = nbh(g, qid, lc);
         for (int i = 0; i < nsel; ++i) {
             if (sel[i] == qid || has_link(ql, sel[i])) continue;
@@ -451,7 +451,7 @@ static int insert_layers(orc_graph* g, uint32_t qid, int l, int lc_min) {
             uint32_t* el = nbh(g, sel[i], lc);
             if (!has_link(el, qid)) el[1 + el[0]++] = qid;
         }
-        /* lines 12-16: shrink overfull neighbourhoods */
+        /* shrink overfull neighbourhoods */
         uint32_t cap = cap_of(g, lc);
         for (int i = 0; i < nsel; ++i) {
             uint32_t e = sel[i];
@@ -468,11 +468,11 @@ static int insert_layers(orc_graph* g, uint32_t qid, int l, int lc_min) {
                 for (int j = 0; j < nn; ++j) el[1 + j] = tmp[j];
             }
         }
-        /* line 17: ep <- W */
+        /* ep <- W */
         for (int i = 0; i < nW; ++i) ep[i] = W[i];
         n_ep = nW;
     }
-    /* lines 18-19 */
+    /* a new top level moves the enter point */
     if (l > L) {
         g->ep = qid;
         g->maxlevel = l;
@@ -612,7 +612,7 @@ static int layer0_batches(orc_graph* g, const uint32_t* ids, uint64_t n_ids, uin
                         cand[n0 + t].id = pairs[i0 + t].src;
                         cand[n0 + t].d = pairs[i0 + t].d;
                     }
-                    /* Alg. 1 lines 13-15: SELECT-NEIGHBORS(e, eConn, Mmax0) over
+                    /* Alg. 1's shrink: SELECT-NEIGHBORS(e, eConn, Mmax0) over
                      * the whole of eConn, old members and new ones */
                     qsort(cand, (size_t)(n0 + nin), sizeof(orc_item), cmp_item);
                     const int nn = select_items(g, row(g, e), e, cand, (int)(n0 + nin), (int)g->Mmax0, 0, out);
@@ -707,15 +707,15 @@ int orc_knn_search(const orc_graph* g, const float* q, int K, int ef,
     int efp = ef > K ? ef : K;                         /* ef' = max(ef, K) */
     orc_item* W = (orc_item*)malloc(sizeof(orc_item) * (size_t)(efp + 2));
     if (!W) return -1;
-    orc_item ep = { dist_vec(g, q, row(g, g->ep)), g->ep };   /* line 2 */
+    orc_item ep = { dist_vec(g, q, row(g, g->ep)), g->ep };   /* the enter point */
     if (st) st->n_dist++;
-    int L = g->maxlevel;                                /* line 3 */
-    for (int lc = L; lc >= 1; --lc) {                   /* lines 4-6 */
+    int L = g->maxlevel;                                /* its level, the top one */
+    for (int lc = L; lc >= 1; --lc) {                   /* greedy descent, ef = 1 */
         search_layer_items(g, q, &ep, 1, 1, lc, W, st);
         ep = W[0];
     }
-    int n = search_layer_items(g, q, &ep, 1, efp, 0, W, st);   /* line 7 */
-    for (int i = 0; i < n && i < K; ++i) { ids[i] = W[i].id; dists[i] = W[i].d; }  /* line 8 */
+    int n = search_layer_items(g, q, &ep, 1, efp, 0, W, st);   /* layer 0 with ef' */
+    for (int i = 0; i < n && i < K; ++i) { ids[i] = W[i].id; dists[i] = W[i].d; }  /* the K nearest of W */
     free(W);
     return 0;
 }

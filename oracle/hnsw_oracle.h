@@ -23,10 +23,10 @@
  *  - keepPrunedConnections defaults to false, extendCandidates to false
  *    (Section 4, text after Alg. 5).
  *  - Levels: l = floor(-ln(u) * mL) with u in (0,1] supplied by the caller,
- *    one u per element in id order (Alg. 1, line 4).
+ *    one u per element in id order (the level draw of Alg. 1).
  *  - The first element becomes the enter point with its drawn level and no
- *    links.  The enter point changes only when l > L (Alg. 1, line 18).
- *  - Alg. 1, line 17 "ep <- W": all elements of W seed the next layer's search.
+ *    links.  The enter point changes only when l > L (Alg. 1, strictly).
+ *  - Alg. 1's "ep <- W" between layers: all elements of W seed the next layer's search.
  *  - No self links and no duplicate links are ever stored.
  *  - Alg. 5 with ef < K runs the layer-0 search with ef' = max(ef, K); missing
  *    results (fewer than K reachable elements) are reported as id 0xFFFFFFFF
@@ -79,7 +79,7 @@ orc_graph* orc_new(const float* data, uint64_t N, uint32_t d, int metric,
                    int heuristic, int extend_candidates, int keep_pruned);
 void orc_free(orc_graph* g);
 
-/* Alg. 1, line 4: l = floor(-ln(u) * mL). */
+/* Alg. 1, the level draw: l = floor(-ln(u) * mL). */
 int orc_level_from_u(double u, double mL);
 
 /* Alg. 1: insert element `id` (its vector is row `id` of the data) at level l. */
@@ -96,13 +96,13 @@ int orc_build(orc_graph* g, const double* u);
  * elements, or with batch = 0 of min(32768, max(64, remaining count at the
  * start), remaining, max(64, inserted / 16)) elements.  For a batch:
  *  1. every element q searches the graph as it stands before the batch:
- *     Alg. 5 with K = ef = efConstruction (Alg. 1 lines 5-9 on layer 0);
- *  2. q's layer-0 list becomes SELECT-NEIGHBORS(q, W, M) (line 10, lines
+ *     Alg. 5 with K = ef = efConstruction (Alg. 1's descent and layer search, on layer 0);
+ *  2. q's layer-0 list becomes SELECT-NEIGHBORS(q, W, M) (Alg. 1's own links
  *     11's forward half), in selection order;
  *  3. each element e selected by batch elements takes them into its list,
  *     in ascending id: appended when they fit within Mmax0, otherwise the list
  *     becomes SELECT-NEIGHBORS(e, eConn, Mmax0) over all of eConn, the old
- *     members and every new one (lines 11-16).
+ *     members and every new one (Alg. 1's reverse links and shrink).
  * Elements of one batch do not see one another; batch = 1 is Alg. 1 applied
  * in the order seed, then the rest.  The batch sizes are a free parameter of
  * this form (the paper's parallel construction fixes none); the growing
@@ -121,7 +121,7 @@ int orc_build_batched_sizes(orc_graph* g, const double* u, uint64_t n_first, con
  * from u[0..n): 1. the new elements of level >= 1 take their layer-0 links
  * in batches as in orc_build_batched, searching through the upper layers as
  * they stand; 2. their upper layers follow one at a time in id order (Alg. 1
- * on layers >= 1, enter point updated by lines 18-19); 3. the new elements of
+ * on layers >= 1, enter point updated as Alg. 1 does); 3. the new elements of
  * level 0 are inserted on layer 0 in batches.  Batches as in
  * orc_build_batched (0: the growing schedule, starting from the elements
  * present). */

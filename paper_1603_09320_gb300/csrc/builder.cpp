@@ -5,7 +5,7 @@
 // points.  Here every element has a spin lock guarding its neighbour lists,
 // and one mutex guards the enter point: an element whose level exceeds the
 // current top level holds it for its whole insertion, so the enter point and
-// the top level change together (Alg. 1 lines 18-19).  Worker threads take
+// the top level change together (Alg. 1's enter-point update).  Worker threads take
 // element ids in increasing order from an atomic counter; with one thread the
 // build is Alg. 1 applied to elements 0..N-1 in order.
 //
@@ -145,7 +145,7 @@ void search_layer(Graph& g, Ctx& cx, const float* q, const std::vector<Item>& ep
     auto& W = cx.W;
     C.clear();
     W.clear();
-    for (const Item& e : ep) {  // lines 1-3
+    for (const Item& e : ep) {  // start: v, C and W hold the enter points
         if (cx.mark[e.id] == cx.epoch) continue;
         cx.mark[e.id] = cx.epoch;
         C.push_back(e);
@@ -153,22 +153,22 @@ void search_layer(Graph& g, Ctx& cx, const float* q, const std::vector<Item>& ep
         W.push_back(e);
         std::push_heap(W.begin(), W.end(), MaxTop());
     }
-    while (!C.empty()) {  // line 4
+    while (!C.empty()) {  // while C is not empty
         std::pop_heap(C.begin(), C.end(), MinTop());
-        Item c = C.back();  // line 5
+        Item c = C.back();  // the nearest of C
         C.pop_back();
-        if (key_less(W.front(), c)) break;  // lines 6-8
+        if (key_less(W.front(), c)) break;  // stop: c is further than the furthest of W
         read_list(g, c.id, lc, cx.nb);
-        for (uint32_t e : cx.nb) {  // line 9
-            if (cx.mark[e] == cx.epoch) continue;  // line 10
-            cx.mark[e] = cx.epoch;                  // line 11
+        for (uint32_t e : cx.nb) {  // each neighbour of c
+            if (cx.mark[e] == cx.epoch) continue;  // visited
+            cx.mark[e] = cx.epoch;                  // mark visited
             Item ei{g.dist(q, g.row(e)), e};
-            if (key_less(ei, W.front()) || W.size() < ef) {  // lines 12-13
+            if (key_less(ei, W.front()) || W.size() < ef) {  // admit: closer than the furthest, or W not full
                 C.push_back(ei);
                 std::push_heap(C.begin(), C.end(), MinTop());
                 W.push_back(ei);
                 std::push_heap(W.begin(), W.end(), MaxTop());
-                if (W.size() > ef) {  // lines 16-17
+                if (W.size() > ef) {  // drop the furthest
                     std::pop_heap(W.begin(), W.end(), MaxTop());
                     W.pop_back();
                 }
@@ -201,9 +201,9 @@ void select_neighbors(Graph& g, Ctx& cx, const float* base, uint32_t base_id, st
         for (size_t i = 0; i < C.size() && R.size() < M; ++i) R.push_back(C[i]);
         return;
     }
-    auto& Wq = cx.tmp;  // working queue, kept sorted (line 2)
+    auto& Wq = cx.tmp;  // working queue, kept sorted
     Wq.assign(C.begin(), C.end());
-    if (g.p.extend_candidates) {  // lines 3-7
+    if (g.p.extend_candidates) {  // extendCandidates
         cx.new_epoch();
         for (const Item& e : C) cx.mark[e.id] = cx.epoch;
         std::vector<uint32_t> adj;
@@ -219,7 +219,7 @@ void select_neighbors(Graph& g, Ctx& cx, const float* base, uint32_t base_id, st
     }
     auto& Wd = cx.Wd;
     Wd.clear();
-    for (size_t i = 0; i < Wq.size() && R.size() < M; ++i) {  // lines 9-14
+    for (size_t i = 0; i < Wq.size() && R.size() < M; ++i) {  // accept when closer to the base than to every element of R
         const Item& e = Wq[i];
         bool good = true;
         for (const Item& r : R)
@@ -232,11 +232,11 @@ void select_neighbors(Graph& g, Ctx& cx, const float* base, uint32_t base_id, st
         else
             Wd.push_back(e);  // discarded, in key order
     }
-    if (g.p.keep_pruned)  // lines 15-17
+    if (g.p.keep_pruned)  // refill R from the discarded, nearest first
         for (size_t i = 0; i < Wd.size() && R.size() < M; ++i) R.push_back(Wd[i]);
 }
 
-// Alg. 1 lines 11-16 for one neighbour e: add q to neighbourhood(e) at lc and
+// Alg. 1's reverse link and shrink for one neighbour e: add q to neighbourhood(e) at lc and
 // shrink it with the selection rule when it exceeds the cap.
 void link_back(Graph& g, Ctx& cx, uint32_t e, uint32_t q, int lc) {
     const uint32_t cap = g.cap(lc);
@@ -288,12 +288,12 @@ void insert(Graph& g, Ctx& cx, uint32_t q) {
     if (l <= L) top.unlock();  // only a new top element keeps the lock
 
     Item cur{g.dist(qv, g.row(ep0)), ep0};
-    for (int lc = L; lc > l; --lc) cur = greedy(g, cx, qv, cur, lc);  // lines 5-7
+    for (int lc = L; lc > l; --lc) cur = greedy(g, cx, qv, cur, lc);  // greedy descent above the element's level
     std::vector<Item> eps{cur};
     std::vector<Item> W;
     const int top_lc = std::min(L, l);
     std::vector<std::vector<Item>> sels(size_t(std::max(top_lc, -1) + 1));
-    for (int lc = top_lc; lc >= 0; --lc) {  // lines 8-17
+    for (int lc = top_lc; lc >= 0; --lc) {  // the element's layers, top down
         search_layer(g, cx, qv, eps, g.p.ef_construction, lc);
         W = cx.W;
         cx.cand.assign(W.begin(), W.end());
@@ -305,9 +305,9 @@ void insert(Graph& g, Ctx& cx, uint32_t q) {
         for (const Item& s : sel)
             if (s.id != q) ql[1 + ql[0]++] = s.id;
         g.locks[q].unlock();
-        eps.swap(W);  // line 17
+        eps.swap(W);  // ep <- W
     }
-    // the reverse links (lines 11-16) once neighbourhood(q) is written on
+    // the reverse links once neighbourhood(q) is written on
     // every layer: q is unreachable until the first of them, so no concurrent
     // insertion can enter layer 0 at q while q's layer-0 list is still empty.
     // Sequentially this is the same graph: a search on layer lc - 1 reads no
@@ -315,7 +315,7 @@ void insert(Graph& g, Ctx& cx, uint32_t q) {
     for (int lc = top_lc; lc >= 0; --lc)
         for (const Item& s : sels[size_t(lc)])
             if (s.id != q) link_back(g, cx, s.id, q, lc);
-    if (l > L) {  // lines 18-19
+    if (l > L) {  // a new top level moves the enter point
         g.ep = q;
         g.maxlevel = l;
     }
@@ -348,7 +348,7 @@ extern "C" hnsw_status hnsw_build(const float* data, uint64_t N, uint32_t d, hns
         for (uint64_t i = 0; i < N; ++i) {
             const double u = level_u[i];
             if (!(u > 0.0 && u <= 1.0)) return fail(HNSW_EINVAL, "hnsw_build: level_u outside (0,1]");
-            const double lv = std::floor(-std::log(u) * p.mL);  // Alg. 1 line 4
+            const double lv = std::floor(-std::log(u) * p.mL);  // the level draw of Alg. 1
             if (lv > 255) return fail(HNSW_EINVAL, "hnsw_build: level above 255");
             g.level[i] = uint8_t(lv);
             g.upoff[i] = rows * (p.Mmax + 1);

@@ -12,9 +12,9 @@
 //     GPU in batches, in id order: for a batch, every element searches the
 //     graph as it stands before the batch (Alg. 5's descent through the upper
 //     layers, then SEARCH-LAYER with ef = efConstruction on layer 0, run by the
-//     library's search kernel), selects its M links (Alg. 4 lines 9-17), and
+//     library's search kernel), selects its M links (Alg. 4's selection), and
 //     the reverse links are added per target element, which shrinks its list
-//     with Alg. 4 when it exceeds Mmax0 (Alg. 1 lines 11-16).
+//     with Alg. 4 when it exceeds Mmax0 (Alg. 1's reverse links and shrink).
 // Elements of one batch do not see one another (they are linked only through
 // the elements they link to); a batch is at most 1/16 of the elements already
 // inserted, so each element searches a graph that already holds at least 94%
@@ -141,10 +141,10 @@ __device__ __forceinline__ float dist_sm(const float (&x)[kMaxDW], const float* 
 // SELECT-NEIGHBORS, resumable: takes the candidates (cid[i], cd[i]), i < nc,
 // sorted by (distance to the base, id) and following every candidate of
 // earlier calls, into R (w.Rid/Rd/Rv; nr entries so far), at most cap.
-// heuristic: Alg. 4 lines 9-14 without extendCandidates (a candidate is
+// heuristic: Alg. 4's acceptance loop without extendCandidates (a candidate is
 // accepted when it is closer to the base than to every element accepted
 // before it, strictly); the discarded ones are recorded in order (nd so far,
-// the first cap of them: lines 15-17 never take more).  Otherwise Alg. 3
+// the first cap of them: keepPrunedConnections never takes more).  Otherwise Alg. 3
 // (the cap nearest).
 __device__ void select_more(const float* rows, uint32_t stride, uint32_t d, uint32_t dp, int metric,
                             const uint32_t* cid, const float* cd, int nc, int cap, bool heuristic,
@@ -187,7 +187,7 @@ __device__ void select_more(const float* rows, uint32_t stride, uint32_t d, uint
     }
 }
 
-// Alg. 4 lines 15-17 (keepPrunedConnections): the nearest discarded
+// Alg. 4's last step (keepPrunedConnections): the nearest discarded
 // candidates fill R up to cap.
 __device__ void append_pruned(const WarpSmem& w, int cap, int& nr, int nd, int lane) {
     for (int i = 0; i < nd && nr < cap; ++i) {
@@ -289,7 +289,7 @@ __device__ __forceinline__ unsigned lanes_below(int lane) { return (1u << lane) 
 // One warp per target element e (a segment of the sorted pairs): the new
 // elements linking to e join neighbourhood(e); when the list then exceeds
 // Mmax0 it becomes SELECT-NEIGHBORS(e, eConn, Mmax0) over all of eConn, the
-// current members and the new ones (Alg. 1 lines 11-16).  Alg. 4 takes eConn
+// current members and the new ones (Alg. 1's reverse links and shrink).  Alg. 4 takes eConn
 // in ascending (distance, id) order and stops once Mmax0 are accepted; here
 // that order is walked in chunks of kKeep: each chunk is the kKeep smallest
 // keys above the previous chunk's last one (keys are distinct: ids are),
@@ -537,7 +537,7 @@ extern "C" hnsw_status hnsw_build_gpu(const float* data, uint64_t N, uint32_t d,
         return fail(HNSW_EINVAL, "hnsw_build_gpu: invalid parameters (d <= 256, efConstruction <= 1024, "
                                  "no extendCandidates)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // levels (Alg. 1 line 4) and the seed: the first elements and every
+    // levels (the level draw of Alg. 1) and the seed: the first elements and every
     // element of level >= 1, in id order
     std::vector<uint8_t> level(N);
     uint64_t rows = 0;
@@ -738,11 +738,11 @@ __device__ __forceinline__ uint32_t* upper_row(const UpperArgs& a, uint32_t e, i
     return const_cast<uint32_t*>(a.v.nbrU) + (uint64_t(a.v.upoff[e]) + uint32_t(lc - 1)) * a.v.sU;
 }
 
-// Alg. 1 lines 5-17 on layers >= 1 for each new element in turn (one warp):
+// Alg. 1's descent and layer insertion on layers >= 1 for each new element in turn (one warp):
 // greedy descent above the element's level, then on each of its layers
 // SEARCH-LAYER with efConstruction, SELECT-NEIGHBORS for its list and the
 // reverse links, shrunk with the same selection beyond Mmax; a new top level
-// makes the element the enter point (lines 18-19).
+// makes the element the enter point (as in Alg. 1).
 __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
         __syncwarp();
         uint32_t cur = ep;
         float dcur = dist_id(xq, rows, stride, d, ep, V.metric, lane);
-        for (int lc = L; lc > l; --lc) {  // lines 5-7, ef = 1 (steepest descent)
+        for (int lc = L; lc > l; --lc) {  // descent above the level, ef = 1 (steepest descent)
             for (;;) {
                 // every neighbour's distance at once (a lane each), then the
                 // smallest key over the warp
@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
         if (lane == 0) Ek[0] = mkkey(dcur, cur);
         __syncwarp();
         for (int lc = l < L ? l : L; lc >= 1; --lc) {
-            // SEARCH-LAYER(q, ep, efc, lc) -- lines 8-9, in the single-list
+            // SEARCH-LAYER(q, ep, efc, lc), in the single-list
             // form: W sorted by key with an 'expanded' bit below the id; its
             // unexpanded entries are C (an element that left W can never be
             // expanded: it lies beyond W's furthest when reached), the next
@@ -840,14 +840,14 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
                         break;
                     }
                 }
-                if (pos < 0) break;  // every entry of W expanded (lines 4-8)
+                if (pos < 0) break;  // every entry of W expanded (Alg. 2 stops)
                 const uint64_t c = Wa[pos];
                 __syncwarp();
                 if (lane == 0) Wa[pos] = c | 1ull;
                 scan = pos + 1;
                 const uint32_t* row = upper_row(a, lid(c), lc);
                 for (uint32_t j0 = 0; j0 < V.Mmax; j0 += 32) {
-                    // lines 9-12 for every neighbour at once, a lane each
+                    // each neighbour's visited test and distance at once, a lane each
                     const uint32_t j = j0 + lane;
                     const uint32_t e = j < V.Mmax ? row[j] : kNone;
                     const bool fresh = e != kNone && a.visited[e] != epoch;
@@ -856,7 +856,7 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
                         a.visited[e] = epoch;
                         k = (uint64_t(f2ord(dist_lane(qs, rows, stride, d, e, V.metric))) << 32) | (uint64_t(e) << 1);
                     }
-                    // lines 13-17: with W full only keys below its furthest enter
+                    // admission: with W full only keys below its furthest enter
                     const bool pass = fresh && (wn < a.efc || k < (Wa[wn - 1] & ~1ull));
                     const unsigned m = __ballot_sync(kFull, pass);
                     if (!m) continue;
@@ -906,7 +906,7 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
             }
             n_ep = int(wn);
             __syncwarp();
-            // neighbourhood(q) at lc -- lines 9-10
+            // neighbourhood(q) at lc: SELECT-NEIGHBORS(q, W, M)
             const int nr = select_links(rows, stride, d, dp, V.metric, Wid, Wd, int(wn), a.M, a.heuristic != 0,
                                         a.keep_pruned != 0, w, lane);
             for (int j = lane; j < nr; j += 32) qR[j] = w.Rid[j];
@@ -914,7 +914,7 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
             uint32_t* rq = upper_row(a, q, lc);
             for (uint32_t j = lane; j < V.Mmax; j += 32) rq[j] = int(j) < nr ? qR[j] : kNone;
             __syncwarp();
-            // reverse links -- lines 11-16
+            // reverse links and their shrink
             for (int t = 0; t < nr; ++t) {
                 const uint32_t r = qR[t];
                 uint32_t* rr = upper_row(a, r, lc);
@@ -953,7 +953,7 @@ __global__ void __launch_bounds__(32) insert_upper(const UpperArgs a) {
                 __syncwarp();
             }
         }
-        if (l > L && lane == 0) {  // lines 18-19
+        if (l > L && lane == 0) {  // a new top level moves the enter point
             a.state[0] = int(q);
             a.state[1] = l;
         }
@@ -1079,7 +1079,7 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
     const int heur = (ix->build_flags & 1u) ? 1 : 0, keep = (ix->build_flags & 4u) ? 1 : 0;
     if ((ix->build_flags & 2u) != 0) return ins_fail(HNSW_EINVAL, "graphs built with extendCandidates");
     if (efc < 1 || efc > 1024) return ins_fail(HNSW_EINVAL, "efConstruction of the graph outside 1..1024");
-    // levels (Alg. 1 line 4) and the new upper rows, in id order
+    // levels (the level draw of Alg. 1) and the new upper rows, in id order
     std::vector<uint8_t> lv(n);
     std::vector<uint32_t> up(n, kNone), U, Z;
     std::vector<uint8_t> Ul;

@@ -4,7 +4,7 @@
 // device work counter until the batch is exhausted (persistent kernel).
 //
 // Per query:
-//   1. greedy ef=1 descent through layers L..1 (Alg. 5 lines 4-6).  Under key
+//   1. greedy ef=1 descent through layers L..1 (Alg. 5's descent).  Under key
 //      order (distance, id), SEARCH-LAYER with ef=1 is steepest descent: move
 //      to the best of the current element's neighbours while it beats the
 //      current element.  No visited set is needed for that.
@@ -12,12 +12,12 @@
 //      shared memory, sorted by key and capped at ef', with an "expanded" bit
 //      per entry instead of the two priority queues: under key order the
 //      unextracted candidates that can still be expanded before the break of
-//      lines 7-8 are exactly the unexpanded entries of W, so "extract the
+//      Alg. 2's stop test are exactly the unexpanded entries of W, so "extract the
 //      nearest of C" is "take the first unexpanded entry" and the loop ends
 //      when none is left.  All unvisited neighbours of the expanded element
 //      are scored together and merged at once; sequential insertion by lines
 //      12-17 leaves the same top-ef' of the union.
-//   3. the K first entries of W (Alg. 5 line 8), or, with rerank, the K best
+//   3. the K first entries of W (Alg. 5's result), or, with rerank, the K best
 //      of W by exact fp32 distance recomputed from the fp32 copy.
 //
 // Visited set: a 4-way bucketed hash of element ids in shared memory; when a
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
                 n_eval = a.up_cnt[2 * uint64_t(qi)];
                 n_stepU = a.up_cnt[2 * uint64_t(qi) + 1];
             } else {
-            // enter point and greedy descent (Alg. 5 lines 2-6)
+            // enter point and greedy descent (Alg. 5)
             if (lane == 0) ids[0] = ix.ep;
             __syncwarp();
             D::run(ix, qr, ids, 1, dst, lane);
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
                         break;
                     }
                 }
-                if (p < 0) {  // every entry of W expanded: lines 7-8
+                if (p < 0) {  // every entry of W expanded: Alg. 2 stops
                     if (nxt_id != kNone) cp_async_wait_all();
                     break;
                 }
@@ -850,7 +850,7 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
                 }
             }
         }
-        // results (Alg. 5 line 8)
+        // results (the K nearest of W, Alg. 5)
         if (a.rerank && size > 0) {
             for (int b = 0; b < size; b += kMaxDeg) {
                 const int nb = min(kMaxDeg, size - b);

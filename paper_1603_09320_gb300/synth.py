@@ -142,7 +142,7 @@ def queries(name: str, n: int | None = None, training: bool = False) -> np.ndarr
 
 
 def level_uniforms(name: str, n: int | None = None) -> np.ndarray:
-    """The u of Alg. 1 line 4 for elements 0..n-1 (seed 3000+c)."""
+    """The u of the level draw of Alg. 1 for elements 0..n-1 (seed 3000+c)."""
     idx, N, *_ = WORKLOADS[name]
     return uniform_open01(3000 + idx, N if n is None else n)
 

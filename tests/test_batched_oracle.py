@@ -198,7 +198,7 @@ def test_explicit_schedule_is_the_default_schedule():
 
 
 def test_shrink_takes_all_of_econn_when_a_list_gets_over_256_new_links():
-    """Alg. 1 lines 13-15 shrink over the whole of eConn.  The hub input sends
+    """Alg. 1 shrinks an overfull list over the whole of eConn.  The hub input sends
     all 301 ray points of one batch to the hub: its list then holds, by
     Alg. 4 worked by hand, the t = 1 point of rays 0..9 (each closer to the
     hub, at 1, than to any other accepted point, at 2; every further point of

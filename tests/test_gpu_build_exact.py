@@ -65,7 +65,7 @@ def test_gpu_insert_equals_batched_oracle():
 def test_gpu_build_shrinks_over_all_of_econn(keep):
     """A batch that sends 301 new links to one list (and to a few filler
     lists): the GPU's reverse-link shrink walks the whole of eConn, as the
-    oracle's batch form does (Alg. 1 lines 13-15), byte for byte."""
+    oracle's batch form does (Alg. 1), byte for byte."""
     import torch
     assert torch.cuda.is_available()
     import _hub

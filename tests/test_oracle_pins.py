@@ -90,7 +90,7 @@ def test_hand_example_search(oracle):
 
 def test_hand_example_trace(oracle):
     # The layer-0 beam of the search above (K=2, ef=2, from p3 at 85), state
-    # after each expansion (Alg. 2 lines 4-17):
+    # after each expansion (the main loop of Alg. 2):
     #   expand p3: p1 (5) joins W, p2 (225) rejected -> W {p1, p3}; 2 evals;
     #              K-th nearest p3 (85) is the first -> stale 0
     #   expand p1: p4 (65) joins, p3 evicted; p5 (65,5) loses to (65,4)
@@ -111,7 +111,7 @@ def test_hand_example_trace(oracle):
 
 
 # --------------------------------------------------------------------------
-# Level distribution (Alg. 1 line 4; Section 4.1 mL = 1/ln M; eq. (1))
+# Level distribution (the level draw of Alg. 1; Section 4.1 mL = 1/ln M; eq. (1))
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("M", [8, 16])
 def test_level_histogram_geometric(oracle, M):
@@ -194,7 +194,7 @@ def test_blob_roundtrip_and_rejects(oracle):
 
 
 # --------------------------------------------------------------------------
-# Alg. 2 with ef=1 == steepest descent (Alg. 5 lines 4-6)
+# Alg. 2 with ef=1 == steepest descent (the descent of Alg. 5)
 # --------------------------------------------------------------------------
 def test_greedy_lemma(oracle):
     from paper_1603_09320_gb300 import synth
@@ -328,7 +328,7 @@ def test_heuristic_1d_gives_line_neighbours(oracle):
 
 
 def test_heuristic_acceptance_properties(oracle):
-    # Alg. 4 lines 9-14: the first candidate is always accepted; every
+    # Alg. 4's acceptance loop: the first candidate is always accepted; every
     # accepted e is strictly closer to the base than to each earlier accepted
     # r; every rejected candidate examined before the last acceptance has an
     # accepted r (examined before it) with d(e,r) <= d(e,base).
@@ -355,7 +355,7 @@ def test_heuristic_acceptance_properties(oracle):
 
 
 def test_extend_candidates_adds_the_candidates_neighbourhoods(oracle):
-    # Alg. 4 lines 3-6: extendCandidates selects over C plus every layer-lc
+    # Alg. 4's extendCandidates step selects over C plus every layer-lc
     # neighbour of an element of C (the base element itself excluded); the
     # union is formed here from the graph's lists and selected without it
     p = {"M": 6, "Mmax": 6, "Mmax0": 12, "efC": 40}
@@ -419,12 +419,12 @@ def test_heuristic_beats_simple_selection_on_clustered_data(oracle):
 
 
 def test_heuristic_tie_is_rejected(oracle):
-    # Alg. 4 line 11 read strictly: e with d(e,base) == d(e,r) is not "closer
+    # Alg. 4's acceptance test read strictly: e with d(e,base) == d(e,r) is not "closer
     # to the base" than r, so it is discarded.
     X = np.array([[1.0, 0.0], [0.5, 2.0]], dtype=np.float32)  # r, e on the bisector
     g = oracle.Graph.new(X, M=2)
     base = np.array([0.0, 0.0], dtype=np.float32)
     assert g.dist(base, 1) == float(((X[1].astype(np.float64) - X[0]) ** 2).sum())
     assert g.select_heuristic(base, [0, 1], 2) == [0]
-    # keepPrunedConnections refills from the discarded queue (lines 15-17)
+    # keepPrunedConnections refills from the discarded queue (Alg. 4's last step)
     assert g.select_heuristic(base, [0, 1], 2, keep_pruned=True) == [0, 1]

@@ -7,9 +7,9 @@ small LOSSY visited set (entries can be overwritten, so an element may be
 evaluated twice).  Claims, under key order:
   * C (not yet extracted) restricted to keys <= the furthest of W is exactly
     the set of unexpanded entries of W, so "extract nearest from C" and the
-    break of lines 7-8 become "take the first unexpanded entry of W, stop if
+    stop test become "take the first unexpanded entry of W, stop if
     there is none";
-  * inserting a batch of neighbours one by one with lines 12-17 leaves the
+  * inserting a batch of neighbours one by one with Alg. 2's admission and eviction leaves the
     top-ef of (W u batch), independent of order;
   * an element evaluated again after the visited set forgot it is either
     already in W (its key is equal to an entry: dropped) or worse than the
