@@ -87,6 +87,31 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 #ifndef HNSW_B16_U
 #define HNSW_B16_U 2
 #endif
+// HNSW_PAIRED_FMA: distances with the paired fp32 operations of sm_100+
+// (two coordinates per fused multiply-add; two partial sums per row, added
+// at the end); for squared L2 the query is held negated, x + (-q) being
+// exactly -(q - x)
+#ifndef HNSW_PAIRED_FMA
+#define HNSW_PAIRED_FMA 0
+#endif
+// HNSW_MIXED_SUB: for bf16 / f16 rows and squared L2, x - q in one
+// mixed-precision subtraction per coordinate (the 16-bit x taken as it is
+// stored, q in fp32, the difference rounded once to fp32: the same value as
+// decoding x to fp32 and subtracting)
+#ifndef HNSW_MIXED_SUB
+#define HNSW_MIXED_SUB 0
+#endif
+
+// x - q for the two 16-bit values of w (low half first), rounded once to fp32
+template <int ST>
+__device__ __forceinline__ void sub_halves(uint32_t w, float q0, float q1, float& t0, float& t1) {
+    if (ST == HNSW_BF16)
+        asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n sub.rn.f32.bf16 %0, l, %3;\n sub.rn.f32.bf16 %1, h, %4;\n}"
+            : "=f"(t0), "=f"(t1) : "r"(w), "f"(q0), "f"(q1));
+    else
+        asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n sub.rn.f32.f16 %0, l, %3;\n sub.rn.f32.f16 %1, h, %4;\n}"
+            : "=f"(t0), "=f"(t1) : "r"(w), "f"(q0), "f"(q1));
+}
 #if HNSW_MIN_BLOCKS > 0
 #define HNSW_SEARCH_BOUNDS __launch_bounds__(128, HNSW_MIN_BLOCKS)
 #else
@@ -258,16 +283,18 @@ struct Dist {
     static constexpr int QF = CPL * CPC;  // query coordinates held per lane
     static constexpr int TEAMS = 32 / TEAM;
     static constexpr int RPR = TEAMS * U;  // rows per round
+    static constexpr bool MIXED = HNSW_MIXED_SUB && (ST == HNSW_BF16 || ST == HNSW_F16);
 
-    __device__ static void load_q(const float* qp, uint32_t d, float (&qr)[QF], int lane) {
+    __device__ static void load_q(const float* qp, uint32_t d, float (&qr)[QF], int lane, int metric) {
         const int tl = lane % TEAM;
+        const float sg = (HNSW_PAIRED_FMA && !MIXED && metric == HNSW_L2SQ) ? -1.0f : 1.0f;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             const int ch = tl + c * TEAM;
 #pragma unroll
             for (int j = 0; j < CPC; ++j) {
                 const uint32_t co = uint32_t(ch * CPC + j);
-                qr[c * CPC + j] = co < d ? qp[co] : 0.0f;
+                qr[c * CPC + j] = co < d ? sg * qp[co] : 0.0f;
             }
         }
     }
@@ -299,6 +326,51 @@ struct Dist {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 float acc = 0.0f;
+                if (MIXED && ix.metric == HNSW_L2SQ) {
+#if HNSW_PAIRED_FMA
+                    float2 acc2 = make_float2(0.0f, 0.0f);
+#endif
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) {
+                        const uint32_t w[4] = {v[u][c].x, v[u][c].y, v[u][c].z, v[u][c].w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float t0, t1;
+                            sub_halves<ST>(w[i], qr[c * CPC + 2 * i], qr[c * CPC + 2 * i + 1], t0, t1);
+#if HNSW_PAIRED_FMA
+                            const float2 t = make_float2(t0, t1);
+                            acc2 = __ffma2_rn(t, t, acc2);
+#else
+                            acc = fmaf(t0, t0, acc);
+                            acc = fmaf(t1, t1, acc);
+#endif
+                        }
+                    }
+#if HNSW_PAIRED_FMA
+                    acc = acc2.x + acc2.y;
+#endif
+                } else {
+#if HNSW_PAIRED_FMA
+                float2 acc2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) {
+                    float x[CPC];
+                    Store<ST>::decode(v[u][c], x);
+#pragma unroll
+                    for (int j = 0; j < CPC; j += 2) {
+                        float2 x2 = make_float2(x[j], x[j + 1]);
+                        if (ST == HNSW_FP8E4M3) x2 = make_float2(x2.x * sc[u], x2.y * sc[u]);
+                        const float2 q2 = make_float2(qr[c * CPC + j], qr[c * CPC + j + 1]);
+                        if (ix.metric == HNSW_L2SQ) {
+                            const float2 t = __fadd2_rn(x2, q2);
+                            acc2 = __ffma2_rn(t, t, acc2);
+                        } else {
+                            acc2 = __ffma2_rn(q2, x2, acc2);
+                        }
+                    }
+                }
+                acc = acc2.x + acc2.y;
+#else
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
                     float x[CPC];
@@ -318,6 +390,8 @@ struct Dist {
                         }
                     }
                 }
+#endif
+                }
 #pragma unroll
                 for (int o = TEAM / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
                 const int r = base + u * TEAMS + team;
@@ -327,29 +401,46 @@ struct Dist {
     }
 };
 
-// exact fp32 distances from the fp32 copy (rerank): teams of 8 lanes, q in smem
+// exact fp32 distances from the fp32 copy (rerank): every row's lines are
+// first requested into L2 (a lane per row), then teams of 8 lanes take a row
+// each, 4 rows per warp round, every chunk a lane reads of its row (up to 32
+// chunks per pass) loaded before any is used; q in shared memory
 __device__ void dist32_rows(const DevIndex& ix, const float* qs, const uint32_t* ids, int n, float* out, int lane) {
     const int team = lane >> 3, tl = lane & 7;
     const uint32_t C = ix.row_chunks32;
+    for (int r = lane; r < n; r += 32) {
+        const uint8_t* rp = reinterpret_cast<const uint8_t*>(ix.vec32 + uint64_t(ids[r]) * C);
+        for (uint32_t b = 0; b < C * 16; b += 128) prefetch_l2(rp + b);
+    }
     const float4* q4 = reinterpret_cast<const float4*>(qs);
     for (int base = 0; base < n; base += 4) {
         const int r = base + team;
         const bool live = r < n;
         const uint4* rowp = ix.vec32 + uint64_t(live ? ids[r] : 0u) * C;
         float acc = 0.0f;
-        for (uint32_t ch = tl; ch < C; ch += 8) {
-            if (!live) break;
-            const uint4 v = ld_row_chunk(rowp + ch);
-            const float4 qq = q4[ch];
-            const float x[4] = {__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w)};
-            const float qv[4] = {qq.x, qq.y, qq.z, qq.w};
+        for (uint32_t cb = 0; cb < C; cb += 32) {
+            uint4 v[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (ix.metric == HNSW_L2SQ) {
-                    const float t = qv[j] - x[j];
-                    acc = fmaf(t, t, acc);
-                } else {
-                    acc = fmaf(qv[j], x[j], acc);
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t ch = cb + uint32_t(tl + 8 * c);
+                v[c] = (live && ch < C) ? ld_row_chunk(rowp + ch) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t ch = cb + uint32_t(tl + 8 * c);
+                if (ch >= C) break;
+                const float4 qq = q4[ch];
+                const float qv[4] = {qq.x, qq.y, qq.z, qq.w};
+                const float x[4] = {__uint_as_float(v[c].x), __uint_as_float(v[c].y), __uint_as_float(v[c].z),
+                                    __uint_as_float(v[c].w)};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (ix.metric == HNSW_L2SQ) {
+                        const float t = qv[j] - x[j];
+                        acc = fmaf(t, t, acc);
+                    } else {
+                        acc = fmaf(qv[j], x[j], acc);
+                    }
                 }
             }
         }
@@ -484,63 +575,55 @@ __device__ int merge_batch(uint64_t* W, int& size, int efp, const uint32_t* ids,
 }
 
 // merge_batch for a list of at most 64 entries and at most 32 new
-// neighbours: W is read into registers (entries lane and lane + 32), each
-// surviving neighbour's position and duplicate test come from two ballots,
-// and every entry is written once to its new position.  Same result as
-// merge_batch.
+// neighbours (a lane each).  Every surviving neighbour finds its lower bound
+// in W by a binary search of its own; one pass over the survivors then gives
+// each its rank among them (its final position is lower bound + rank) and
+// each W entry the number of survivors placed before it; W is read into
+// registers (entries lane and lane + 32) before any write, and every entry is
+// written once.  Same result as merge_batch.
 __device__ int merge_small(uint64_t* W, int& size, int efp, const uint32_t* ids, const float* dst, int n,
                            int lane) {
-    const uint64_t w0 = lane < size ? W[lane] : ~0ull;
-    const uint64_t w1 = lane + 32 < size ? W[lane + 32] : ~0ull;
-    const uint64_t a0 = w0 >> 1, a1 = w1 >> 1;  // keys without the expanded bit
+    const uint64_t w0 = lane < size ? W[lane] : 0ull;
+    const uint64_t w1 = lane + 32 < size ? W[lane + 32] : 0ull;
     const bool full = size >= efp;
-    uint64_t wlast = 0;
-    if (size > 0) {
-        const int t = size - 1;
-        wlast = __shfl_sync(kFull, t >= 32 ? a1 : a0, t & 31);
-    }
-    uint64_t k = 0;
+    const uint64_t wlast = size > 0 ? (W[size - 1] >> 1) : 0ull;
+    uint64_t k = 0, k1 = 0;
     bool ok = false;
+    int lb = 0;
     if (lane < n) {
         k = mkkey(dst[lane], ids[lane]);
-        ok = !(full && (k >> 1) > wlast);
+        k1 = k >> 1;
+        ok = !(full && k1 > wlast);
+        if (ok) {
+#pragma unroll
+            for (int step = 32; step > 0; step >>= 1)  // entries of W below k1
+                if (lb + step <= size && (W[lb + step - 1] >> 1) < k1) lb += step;
+            if (lb < size && (W[lb] >> 1) == k1) ok = false;  // already in W
+        }
     }
     const uint32_t surv = __ballot_sync(kFull, ok);
     if (surv == 0) return INT_MAX;
-    const uint64_t k1 = k >> 1;
-    int cnt0 = 0, cnt1 = 0;  // new entries placed before my W entries
-    int mylb = 0, myrank = 0;
-    bool mine_dup = false;
-    int m = 0;
+    int rank = 0, c0 = 0, c1 = 0;  // survivors below my key; placed before my W entries
     for (uint32_t bits = surv; bits; bits &= bits - 1) {
         const int sl = __ffs(bits) - 1;
         const uint64_t ks = __shfl_sync(kFull, k1, sl);
-        const bool dup = __any_sync(kFull, a0 == ks || a1 == ks);  // already in W
-        if (dup) {
-            if (lane == sl) mine_dup = true;
-            continue;
-        }
-        ++m;
-        cnt0 += a0 != (~0ull >> 1) && ks < a0;
-        cnt1 += a1 != (~0ull >> 1) && ks < a1;
-        const int lb = __popc(__ballot_sync(kFull, lane < size && a0 < ks)) +
-                       __popc(__ballot_sync(kFull, lane + 32 < size && a1 < ks));
-        if (lane == sl) mylb = lb;
-        if (ok && ks < k1) ++myrank;
+        const int ls = __shfl_sync(kFull, lb, sl);
+        rank += ks < k1;
+        c0 += ls <= lane;
+        c1 += ls <= lane + 32;
     }
     __syncwarp();
-    if (m == 0) return INT_MAX;
-    if (lane < size && lane + cnt0 < efp) W[lane + cnt0] = w0;
-    if (lane + 32 < size && lane + 32 + cnt1 < efp) W[lane + 32 + cnt1] = w1;
+    if (lane < size && lane + c0 < efp) W[lane + c0] = w0;
+    if (lane + 32 < size && lane + 32 + c1 < efp) W[lane + 32 + c1] = w1;
     int pos = INT_MAX;
-    if (ok && !mine_dup) {
-        pos = mylb + myrank;
+    if (ok) {
+        pos = lb + rank;
         if (pos < efp)
             W[pos] = k;
         else
             pos = INT_MAX;
     }
-    size = min(efp, size + m);
+    size = min(efp, size + __popc(surv));
     __syncwarp();
     return int(__reduce_min_sync(kFull, uint32_t(pos)));
 }
@@ -646,7 +729,7 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
             efq = max(int(v & 0xffffu), int(v >> 16));
         }
         float qr[D::QF];
-        D::load_q(qp, ix.d, qr, lane);
+        D::load_q(qp, ix.d, qr, lane, ix.metric);
         if (a.rerank)
             for (uint32_t i = lane; i < ix.row_chunks32 * 4; i += 32) qs[i] = i < ix.d ? qp[i] : 0.0f;
         for (int i = lane; i < (hsz >> 2); i += 32)
