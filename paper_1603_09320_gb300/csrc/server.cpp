@@ -461,6 +461,26 @@ extern "C" hnsw_status hnsw_server_wait(hnsw_server* sv, uint64_t ticket, int32_
     return HNSW_OK;
 }
 
+extern "C" hnsw_status hnsw_server_cancel(hnsw_server* sv, uint64_t ticket) {
+    if (!sv) return fail(HNSW_EINVAL, "hnsw_server_cancel: null server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return fail(HNSW_EINVAL, "hnsw_server_cancel: unknown ticket");
+    Request* rq = it->second.get();
+    auto pit = std::find(sv->pending.begin(), sv->pending.end(), rq);
+    if (rq->complete || pit == sv->pending.end())
+        return fail(HNSW_EBUSY, "hnsw_server_cancel: the request is already admitted or complete");
+    sv->pending.erase(pit);
+    sv->stats.queued--;
+    sv->stats.cancelled++;
+    rq->status = HNSW_ECANCELED;
+    rq->error = "cancelled before admission";
+    rq->finished = Clock::now();
+    rq->complete = true;
+    sv->done_cv.notify_all();
+    return HNSW_OK;
+}
+
 extern "C" hnsw_status hnsw_server_get_stats(hnsw_server* sv, hnsw_server_stats* out) {
     if (!sv || !out) return fail(HNSW_EINVAL, "hnsw_server_get_stats: null argument");
     std::lock_guard<std::mutex> lk(sv->mu);

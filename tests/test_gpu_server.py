@@ -105,3 +105,36 @@ def test_replay_equals_alone(setup):
         ai, ad = ixs[w].search(q, k, ef, rerank=rr)
         np.testing.assert_array_equal(ids, ai)
         np.testing.assert_array_equal(ds, ad)
+
+
+def test_wait_timeout_and_cancel(setup):
+    """Host-side failure paths: a bounded wait on a request still running
+    returns HNSW_ETIMEOUT and leaves the request to complete; a request still
+    queued behind it is cancelled (its wait returns HNSW_ECANCELED and its
+    buffers are not written); an admitted request cannot be cancelled."""
+    hnsw, ixs, Qs = setup
+    sv = hnsw.Server(n_slots=1)
+    a, b = sv.add_index(ixs[1]), sv.add_index(ixs[0])
+    big = np.ascontiguousarray(np.tile(Qs[1], (25, 1)))  # 50,000 queries at ef 512: many milliseconds
+    ta = sv.submit(a, big, 10, 512)
+    tb = sv.submit(b, Qs[0][:100], 10, 32)  # another index: never grouped with ta, queued behind it
+    with pytest.raises(hnsw.HnswError) as e:
+        sv.wait(ta, timeout_ms=0)
+    assert e.value.status == 5  # HNSW_ETIMEOUT; ta is still owned by the server
+    sv.cancel(tb)
+    with pytest.raises(hnsw.HnswError) as e:
+        sv.cancel(ta)  # admitted: on the device
+    assert e.value.status == 6
+    st = sv.stats()
+    assert st["cancelled"] == 1 and st["queued"] == 0
+    with pytest.raises(hnsw.HnswError) as e:
+        sv.wait(tb)
+    assert e.value.status == 7  # HNSW_ECANCELED
+    ids, ds, _ = sv.wait(ta)
+    ai, ad = _alone(ixs[1], big[:500], 10, 512, False)
+    np.testing.assert_array_equal(ids[:500], ai)
+    np.testing.assert_array_equal(ds[:500], ad)
+    with pytest.raises(hnsw.HnswError) as e:
+        sv.cancel(ta)  # consumed
+    assert e.value.status == 1
+    sv.close()
