@@ -44,7 +44,8 @@ typedef enum {
     HNSW_ECUDA = 3,    /* a CUDA call or kernel launch failed (message has the CUDA error) */
     HNSW_ECORRUPT = 4, /* a graph blob failed validation (magic, checksum, links, levels) */
     HNSW_ETIMEOUT = 5, /* a bounded device-side wait ran out */
-    HNSW_EBUSY = 6     /* resource in use (e.g. server queue full) */
+    HNSW_EBUSY = 6,    /* resource in use (e.g. server queue full, request already on the device) */
+    HNSW_ECANCELED = 7 /* the request was cancelled before it reached the device */
 } hnsw_status;
 
 typedef enum { HNSW_L2SQ = 0, HNSW_COSINE = 1 } hnsw_metric;
@@ -244,7 +245,10 @@ typedef struct {
     uint32_t n_exp0;    /* layer-0 expansions (elements taken from C) */
     uint32_t n_stepU;   /* elements expanded on layers >= 1 */
     uint32_t flags;     /* bit0: visited set overflowed (lossy, results unaffected);
-                           bit1: stopped early by the learned stop */
+                           bit1: stopped early by the learned stop;
+                           bit2: the bounds-checked search met an element id, upper-row
+                           index or work index out of range and left this query's
+                           search there (its results are what W held) */
 } hnsw_query_stats;
 
 typedef struct {
@@ -265,7 +269,14 @@ typedef struct {
                                 decreasing descent distance (long searches start first,
                                 results unchanged; uses stream-ordered scratch);
                                 1: one pass in input order; 2: always two passes */
-    int32_t reserved;
+    int32_t check_bounds;    /* 1: the bounds-checked search -- every element id read from
+                                the graph is checked against N and every upper-row index
+                                against the rows allocated before it is used; a query
+                                that meets a bad one leaves its search and sets stats
+                                flag bit 2 (no device fault).  Slower; for diagnosing a
+                                suspect index.  Built for f32 rows of up to 32 chunks and
+                                bf16 rows of up to 16 (d <= 128); other storage, or with
+                                the learned stop: HNSW_EINVAL */
 } hnsw_search_params;
 
 /* hnsw_search with the options above and optional per-query counters
@@ -419,6 +430,7 @@ typedef struct {
     uint64_t submitted, completed, failed;
     uint64_t queued, in_flight;          /* waiting for admission / on the device */
     uint64_t bytes_in_use, budget;       /* device arena */
+    uint64_t cancelled;                  /* removed from the queue by hnsw_server_cancel */
 } hnsw_server_stats;
 
 hnsw_status hnsw_server_create(const hnsw_server_params* params, hnsw_server** out);
@@ -433,6 +445,13 @@ hnsw_status hnsw_server_poll(hnsw_server* server, uint64_t ticket, int32_t* done
  * NULL) receives submit-to-completion time.  A request that failed on the
  * device returns its error here. */
 hnsw_status hnsw_server_wait(hnsw_server* server, uint64_t ticket, int32_t timeout_ms, double* latency_ms);
+/* Cancels a request that is still waiting for admission: it leaves the queue,
+ * its device work is never issued and its output buffers are not written;
+ * hnsw_server_wait on its ticket then returns HNSW_ECANCELED (and consumes
+ * the ticket).  A request already admitted (its launch may be on the device)
+ * or complete is not cancelled: HNSW_EBUSY.  Errors: HNSW_EINVAL (null
+ * server, unknown ticket), HNSW_EBUSY. */
+hnsw_status hnsw_server_cancel(hnsw_server* server, uint64_t ticket);
 hnsw_status hnsw_server_get_stats(hnsw_server* server, hnsw_server_stats* out);
 /* Completes every submitted request, then releases the server's streams and
  * arena. */

@@ -1054,6 +1054,7 @@ extern "C" hnsw_status hnsw_reserve(hnsw_index* ix, uint64_t capacity, void* str
         ix->dev.vec32 = static_cast<const uint4*>(ix->d_vec32);
         ix->dev.nbr0 = static_cast<const uint32_t*>(n0[0]);
         ix->dev.upoff = static_cast<const uint32_t*>(uo[0]);
+        ix->dev.urows = uint32_t(ucap);
         ix->dev.nbrU = static_cast<const uint32_t*>(nu[0]);
     }
     std::lock_guard<std::mutex> il(ix->dev_mu);
@@ -1136,6 +1137,7 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
     V.nbr0 = static_cast<const uint32_t*>(ix->v_nbr0[ina]);
     V.upoff = static_cast<const uint32_t*>(ix->v_upoff[ina]);
     V.nbrU = static_cast<const uint32_t*>(ix->v_nbrU[ina]);
+    V.urows = uint32_t(ix->upper_capacity);
     V.N = uint32_t(N0 + n);
     if (V.storage != HNSW_F32) {
         V.vec = V.vec32;
@@ -1202,6 +1204,7 @@ extern "C" hnsw_status hnsw_insert(hnsw_index* ix, const float* data, uint64_t n
         ix->dev.nbr0 = V.nbr0;
         ix->dev.upoff = V.upoff;
         ix->dev.nbrU = V.nbrU;
+        ix->dev.urows = V.urows;
         ix->dev.N = V.N;
         ix->dev.ep = V.ep;
         ix->dev.maxlevel = V.maxlevel;

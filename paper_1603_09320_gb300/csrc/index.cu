@@ -189,6 +189,7 @@ hnsw_status upload_index(const void* graph_blob, uint64_t blob_bytes, hnsw_dtype
     D.upoff = static_cast<const uint32_t*>(ix->d_upoff);
     D.nbrU = static_cast<const uint32_t*>(ix->d_nbrU);
     D.N = uint32_t(N);
+    D.urows = uint32_t(h.n_upper_rows);
     D.d = d;
     D.row_chunks = row_bytes / 16;
     D.row_chunks32 = d_pad32 / 4;

@@ -39,6 +39,7 @@ struct DevIndex {
     const uint32_t* upoff;
     const uint32_t* nbrU;
     uint32_t N, d;
+    uint32_t urows;  // upper-layer rows allocated (bound of upoff[i] + lc - 1)
     uint32_t row_chunks, row_chunks32;
     uint32_t s0, sU, Mmax0, Mmax;
     uint32_t ep;

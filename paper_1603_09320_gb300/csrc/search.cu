@@ -69,6 +69,19 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 #ifndef HNSW_MIN_BLOCKS
 #define HNSW_MIN_BLOCKS 0
 #endif
+// HNSW_STOP_GLOBAL: STOP launches read the stop network from global memory
+// (10.3 KB, held in L1 by every SM that uses it) and run the plain search's
+// 128-thread blocks, so that consecutive launches still share the SMs; 0: one
+// shared-memory copy of the network per block and large blocks
+#ifndef HNSW_STOP_GLOBAL
+#define HNSW_STOP_GLOBAL 1
+#endif
+// HNSW_STOP_SKIP_IMPROVING: outside trace recording, a due check is put off
+// while the expansion just done changed the K nearest of W (the search is
+// still improving its answer), to the first later expansion that does not
+#ifndef HNSW_STOP_SKIP_IMPROVING
+#define HNSW_STOP_SKIP_IMPROVING 1
+#endif
 // HNSW_STOP_NOINLINE: the stop check (features + network) as a called
 // function instead of inline code in the layer-0 loop
 #ifndef HNSW_STOP_NOINLINE
@@ -99,7 +112,7 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 // stored, q in fp32, the difference rounded once to fp32: the same value as
 // decoding x to fp32 and subtracting)
 #ifndef HNSW_MIXED_SUB
-#define HNSW_MIXED_SUB 0
+#define HNSW_MIXED_SUB 1
 #endif
 
 // x - q for the two 16-bit values of w (low half first), rounded once to fp32
@@ -670,7 +683,7 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 #pragma unroll
     for (int i = 1; i < kStopIn; ++i) fv = lane == i ? f[i] : fv;
     if (lane < kStopIn) aux[4 + lane] = fv;
-    return model ? stop_logit(model, f, hs, lane) : 0.0f;
+    return model ? stop_logit<HNSW_STOP_GLOBAL != 0>(model, f, hs, lane) : 0.0f;
 }
 
 // STOP builds copy the stop network to shared memory once per block, so they
@@ -680,13 +693,33 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 template <int ST, int CPL>
 constexpr bool stop_wide_regs() { return ST == HNSW_F32 && CPL == 4; }
 
+// Resident 128-thread blocks per SM that each plain instantiation's register
+// budget is set for (65,536 registers / (128 x blocks) per thread): 8 (64
+// registers) where the kernel fits without spilling, fewer where its rows in
+// flight need more (fp32 128-d: 72; fp8 with 8 rows per team: about 96; f16
+// with 4 rows per team: about 80).  Without an explicit count the compiler
+// chose budgets that spilled.
+template <int ST, int CPL, int U>
+constexpr int plain_min_blocks() {
+    return (ST == HNSW_F32 && CPL == 4) ? 7 : (ST == HNSW_FP8E4M3 && U == 8) ? 5 : (ST == HNSW_F16 && U == 4) ? 6 : 8;
+}
+
 #ifndef HNSW_STOP_THREADS
 #define HNSW_STOP_THREADS 1024
 #endif
 
-template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP>
-__global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW_STOP_THREADS) : 128,
-                                  STOP ? (stop_wide_regs<ST, CPL>() ? 3 : 1) : 0) hnsw_search_kernel(const SearchArgs a) {
+// CHECK: the bounds-checked build (hnsw_search_params.check_bounds): every
+// element id read from the graph is tested against N and every upper-row
+// index against the rows allocated before any use; a query that meets a bad
+// one sets stats flag bit 2 and leaves its search (its results are what W
+// holds), with no device fault and no trap.
+template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP, bool CHECK = false>
+__global__ void __launch_bounds__(
+    (STOP && !HNSW_STOP_GLOBAL) ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW_STOP_THREADS) : 128,
+    STOP ? (HNSW_STOP_GLOBAL ? (stop_wide_regs<ST, CPL>() ? 6 : plain_min_blocks<ST, CPL, U>())
+                             : (stop_wide_regs<ST, CPL>() ? 3 : 1))
+         : plain_min_blocks<ST, CPL, U>())
+    hnsw_search_kernel(const SearchArgs a) {
     using D = Dist<ST, TEAM, CPL, U, FULL>;
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -708,7 +741,7 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
     const int hsz = 1 << a.hlog;
     // the stop network, one copy per block after the warps' regions (its
     // address is recomputed at each check rather than held in registers)
-    if (STOP && a.stop) {
+    if (STOP && !HNSW_STOP_GLOBAL && a.stop) {
         uint4* d4 = reinterpret_cast<uint4*>(smem + (blockDim.x >> 5) * a.warp_smem);
         const uint4* src = reinterpret_cast<const uint4*>(a.stop);
         for (int i = threadIdx.x; i < int(sizeof(StopDev) / 16); i += blockDim.x) d4[i] = src[i];
@@ -738,7 +771,8 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
         if (STOP && lane == 0) *n_checks = 0;
         int size = 0;
         __syncwarp();
-        if (ix.N > 0) {
+        bool bad = CHECK && ix.N > 0 && !(ix.ep < ix.N);  // bounds-checked build: a bad id or row met
+        if (ix.N > 0 && !bad) {
             uint64_t cur = 0;
             if (a.mode == 2) {  // the descent ran in the first pass
                 cur = a.ep_keys[qi];
@@ -752,20 +786,32 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
             __syncwarp();
             cur = mkkey(dst[0], ix.ep);
             n_eval = 1;
-            for (int lc = ix.maxlevel; lc >= 1; --lc) {
+            for (int lc = ix.maxlevel; lc >= 1 && !bad; --lc) {
                 for (;;) {
                     const uint32_t c = key_id(cur);
                     const uint64_t row = uint64_t(__ldg(ix.upoff + c)) + uint64_t(lc - 1);
+                    if (CHECK && !(row < ix.urows)) {  // c absent from layer lc, or a bad offset
+                        bad = true;
+                        break;
+                    }
                     const uint32_t* urow = ix.nbrU + row * ix.sU;
                     int n = 0;
                     __syncwarp();
                     for (int h = 0; h < int(ix.Mmax); h += 32) {
                         const int j = h + lane;
-                        const uint32_t e = j < int(ix.Mmax) ? __ldg(urow + j) : kNone;
+                        uint32_t e = j < int(ix.Mmax) ? __ldg(urow + j) : kNone;
+                        if (CHECK && e != kNone && !(e < ix.N)) {
+                            bad = true;
+                            e = kNone;
+                        }
                         const bool v = e != kNone;
                         const unsigned m = __ballot_sync(kFull, v);
                         if (v) ids[n + __popc(m & lanemask_lt())] = e;
                         n += __popc(m);
+                    }
+                    if (CHECK && __any_sync(kFull, bad)) {
+                        bad = true;
+                        break;
                     }
                     __syncwarp();
                     D::run(ix, qr, ids, n, dst, lane);
@@ -811,6 +857,7 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
             uint32_t nxt_id = kNone;  // element whose neighbour row is staged in nbuf
             __syncwarp();
             for (;;) {
+                if (CHECK && bad) break;  // the descent met a bad id or row: W holds its last element
                 int p = -1;
                 for (int s = scan; s < size; s += 32) {
                     const int i = s + lane;
@@ -846,6 +893,11 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
                     if (deg > 32) e1 = lane + 32 < deg ? __ldg(nrow + 32 + lane) : kNone;
                 }
                 __syncwarp();
+                if (CHECK && __any_sync(kFull, (e0 != kNone && !(e0 < ix.N)) || (e1 != kNone && !(e1 < ix.N)))) {
+                    bad = true;  // no copy is in flight here: the staged row was waited for above
+                    nxt_id = kNone;
+                    break;
+                }
 #if HNSW_PREFETCH_NEXT
                 // the next unexpanded entry after p is expanded next unless this
                 // batch inserts a better element: stage its neighbour row now
@@ -904,12 +956,18 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
                     // saturating at 65535
                     stale_cd = first_new < kq ? (stale_cd & 0xffffu) : __vaddus2(stale_cd, 0x10000u);
                     stale_cd -= 1u;
-                    const bool check = (stale_cd & 0xffffu) == 0u;
+                    bool check = (stale_cd & 0xffffu) == 0u;
+                    if (HNSW_STOP_SKIP_IMPROVING && check && !a.tr_count && first_new < kq) {
+                        check = false;  // put off to the next expansion
+                        stale_cd |= 1u;
+                    }
                     if (check) stale_cd |= uint32_t(a.stop_period);
                     if (size >= kq && check) {
                         __syncwarp();
                         const StopDev* model =
-                            a.stop ? reinterpret_cast<const StopDev*>(smem + (blockDim.x >> 5) * a.warp_smem) : nullptr;
+                            !a.stop ? nullptr
+                            : HNSW_STOP_GLOBAL ? a.stop
+                                               : reinterpret_cast<const StopDev*>(smem + (blockDim.x >> 5) * a.warp_smem);
                         const float logit = stop_check(model, W, size, kq, aux, n_eval - __float_as_uint(aux[2]),
                                                        stale_cd >> 16, reinterpret_cast<float*>(ck), lane);
                         if (a.tr_count) {
@@ -961,6 +1019,7 @@ __global__ void __launch_bounds__(STOP ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW
             a.out_ids[obase + i] = oid;
             a.out_dists[obase + i] = od;
         }
+        if (CHECK && bad) flags |= 4u;
         if (STOP && a.tr_count && lane == 0) a.tr_count[qi] = int(min(*n_checks, uint32_t(a.tr_max)));
         if (a.stats && lane == 0) {
             hnsw_query_stats s;
@@ -1055,6 +1114,22 @@ bool choose_kernel(int storage, uint32_t chunks, bool stop, KernelChoice& kc) {
     return false;
 }
 
+// The bounds-checked build, for f32 rows of up to 32 chunks and bf16 rows of
+// up to 16 (d <= 128 either way).
+template <int ST, int TEAM, int CPL, int U>
+KernelChoice pick_checked(uint32_t chunks) {
+    if (chunks == uint32_t(TEAM * CPL))
+        return {hnsw_search_kernel<ST, TEAM, CPL, U, true, false, true>, "hnsw_search_kernel (checked)"};
+    return {hnsw_search_kernel<ST, TEAM, CPL, U, false, false, true>, "hnsw_search_kernel (checked)"};
+}
+
+bool choose_kernel_checked(int storage, uint32_t chunks, KernelChoice& kc) {
+    if (storage == HNSW_F32 && chunks <= 8) { kc = pick_checked<HNSW_F32, 8, 1, 8>(chunks); return true; }
+    if (storage == HNSW_F32 && chunks <= 32) { kc = pick_checked<HNSW_F32, 8, 4, HNSW_F32_U>(chunks); return true; }
+    if (storage == HNSW_BF16 && chunks <= 16) { kc = pick_checked<HNSW_BF16, 8, 2, HNSW_B16_U>(chunks); return true; }
+    return false;
+}
+
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes at;
@@ -1090,8 +1165,13 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
                                const uint64_t* q_out = nullptr, const DevIndex* view = nullptr) {
     const DevIndex D = view ? *view : dev_snapshot(ix);
     KernelChoice kc;
-    if (!choose_kernel(D.storage, D.row_chunks, stop != nullptr && stop->period > 0, kc))
+    if (p.check_bounds) {
+        if (stop != nullptr) return fail(HNSW_EINVAL, "search: check_bounds with the learned stop or a trace");
+        if (!choose_kernel_checked(D.storage, D.row_chunks, kc))
+            return fail(HNSW_EINVAL, "search: check_bounds is built for f32 rows of d <= 128 and bf16 of d <= 128");
+    } else if (!choose_kernel(D.storage, D.row_chunks, stop != nullptr && stop->period > 0, kc)) {
         return fail(HNSW_EINVAL, "search: unsupported row size");
+    }
     SearchArgs a{};
     a.ix = D;
     a.q = q;
@@ -1125,9 +1205,9 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
                             size_t(D.row_chunks32) * 16 + kMaxDeg * 4 + 64;
     a.warp_smem = int((per_warp + 15) & ~size_t(15));
     const bool stop_build = stop != nullptr && stop->period > 0;
-    const size_t model_smem = (stop_build && stop->stop) ? sizeof(StopDev) : 0;
+    const size_t model_smem = (!HNSW_STOP_GLOBAL && stop_build && stop->stop) ? sizeof(StopDev) : 0;
     int warps = 4;
-    if (stop_build) {
+    if (stop_build && !HNSW_STOP_GLOBAL) {
         cudaFuncAttributes fa{};
         cudaError_t e = cudaFuncGetAttributes(&fa, kc.fn);
         if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("search: attributes: ") + cudaGetErrorString(e));
@@ -1327,8 +1407,8 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     // schedule: 0 automatic (two passes when the batch exceeds the resident
     // warps), 1 one pass in input order, 2 always two passes
     const DevIndex snap = dev_snapshot(ix);  // both passes search the same version
-    const bool two =
-        snap.N > 0 && (p->schedule == 2 || (p->schedule == 0 && uint64_t(n) > 4ull * resident_warps(ix)));
+    const bool two = snap.N > 0 && !p->check_bounds &&
+                     (p->schedule == 2 || (p->schedule == 0 && uint64_t(n) > 4ull * resident_warps(ix)));
     hnsw_status r = HNSW_OK;
     if (!two) {
         r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 0, nullptr, nullptr, nullptr,

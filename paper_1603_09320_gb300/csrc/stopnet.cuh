@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 namespace hnswgb {
 
@@ -37,33 +38,64 @@ struct StopDev {
 };
 static_assert(sizeof(StopDev) % 16 == 0, "StopDev is copied in 16-byte words");
 
+// Loads of the network's weights.  From global memory (GLOBAL) they are
+// marked L1::evict_last (HNSW_STOP_EVICT_LAST), so that the 10 KB network
+// stays in an SM's L1 while the search streams vector rows through it; from
+// shared memory they are plain loads.
+#ifndef HNSW_STOP_EVICT_LAST
+#define HNSW_STOP_EVICT_LAST 1
+#endif
+template <bool GLOBAL>
+__device__ __forceinline__ float ldw(const float* p) {
+    if (GLOBAL && HNSW_STOP_EVICT_LAST) {
+        float v;
+        asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+    }
+    if (GLOBAL) return __ldg(p);
+    return *p;
+}
+template <bool GLOBAL>
+__device__ __forceinline__ __half2 ldw(const __half2* p) {
+    if (GLOBAL && HNSW_STOP_EVICT_LAST) {
+        uint32_t v;
+        asm("ld.global.nc.L1::evict_last.b32 %0, [%1];" : "=r"(v) : "l"(p));
+        __half2 h;
+        memcpy(&h, &v, 4);
+        return h;
+    }
+    if (GLOBAL) return __ldg(p);
+    return *p;
+}
+
 // Logit of the network for features f (identical in every lane), computed by
-// one warp from the block's shared-memory copy m of the network: lane l owns
-// hidden units l and l + 32.  The first hidden layer is exchanged through a
-// 64-float scratch `hs` in shared memory and read back with 16-byte
-// broadcast loads.
+// one warp from the network m (in global memory when GLOBAL, else the
+// block's shared-memory copy): lane l owns hidden units l and l + 32.  The
+// first hidden layer is exchanged through a 64-float scratch `hs` in shared
+// memory and read back with 16-byte broadcast loads.
+template <bool GLOBAL>
 __device__ __forceinline__ float stop_logit(const StopDev* __restrict__ m, const float (&f)[kStopIn],
                                             float* hs, int lane) {
-    float ha = m->b1[lane], hb = m->b1[lane + 32];
+    float ha = ldw<GLOBAL>(m->b1 + lane), hb = ldw<GLOBAL>(m->b1 + lane + 32);
 #pragma unroll
     for (int i = 0; i < kStopIn; ++i) {
-        ha = fmaf(m->w1[lane * kStopIn + i], f[i], ha);
-        hb = fmaf(m->w1[(lane + 32) * kStopIn + i], f[i], hb);
+        ha = fmaf(ldw<GLOBAL>(m->w1 + lane * kStopIn + i), f[i], ha);
+        hb = fmaf(ldw<GLOBAL>(m->w1 + (lane + 32) * kStopIn + i), f[i], hb);
     }
     __syncwarp();
     hs[lane] = fmaxf(ha, 0.0f);
     hs[lane + 32] = fmaxf(hb, 0.0f);
     __syncwarp();
     // two accumulators per output (even and odd inputs) halve the FMA chains
-    float za = m->b2[lane], zb = m->b2[lane + 32], za1 = 0.0f, zb1 = 0.0f;
+    float za = ldw<GLOBAL>(m->b2 + lane), zb = ldw<GLOBAL>(m->b2 + lane + 32), za1 = 0.0f, zb1 = 0.0f;
     const float4* h4 = reinterpret_cast<const float4*>(hs);
 #pragma unroll 4
     for (int u4 = 0; u4 < kStopH / 4; ++u4) {
         const float4 h = h4[u4];
-        const float2 w0 = __half22float2(m->w2p[(u4 * 4 + 0) * 32 + lane]);
-        const float2 w1 = __half22float2(m->w2p[(u4 * 4 + 1) * 32 + lane]);
-        const float2 w2 = __half22float2(m->w2p[(u4 * 4 + 2) * 32 + lane]);
-        const float2 w3 = __half22float2(m->w2p[(u4 * 4 + 3) * 32 + lane]);
+        const float2 w0 = __half22float2(ldw<GLOBAL>(m->w2p + (u4 * 4 + 0) * 32 + lane));
+        const float2 w1 = __half22float2(ldw<GLOBAL>(m->w2p + (u4 * 4 + 1) * 32 + lane));
+        const float2 w2 = __half22float2(ldw<GLOBAL>(m->w2p + (u4 * 4 + 2) * 32 + lane));
+        const float2 w3 = __half22float2(ldw<GLOBAL>(m->w2p + (u4 * 4 + 3) * 32 + lane));
         za = fmaf(w0.x, h.x, za);
         zb = fmaf(w0.y, h.x, zb);
         za1 = fmaf(w1.x, h.y, za1);
@@ -75,10 +107,10 @@ __device__ __forceinline__ float stop_logit(const StopDev* __restrict__ m, const
     }
     za += za1;
     zb += zb1;
-    float o = m->w3[lane] * fmaxf(za, 0.0f) + m->w3[lane + 32] * fmaxf(zb, 0.0f);
+    float o = ldw<GLOBAL>(m->w3 + lane) * fmaxf(za, 0.0f) + ldw<GLOBAL>(m->w3 + lane + 32) * fmaxf(zb, 0.0f);
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
-    return o + m->b3;
+    return o + ldw<GLOBAL>(&m->b3);
 }
 
 }  // namespace hnswgb

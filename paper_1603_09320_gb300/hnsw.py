@@ -19,7 +19,7 @@ L2SQ, COSINE = 0, 1
 F32, BF16, FP8E4M3, F16 = 0, 1, 2, 3
 DTYPES = {"f32": F32, "bf16": BF16, "fp8": FP8E4M3, "f16": F16}
 
-STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECORRUPT", 5: "ETIMEOUT", 6: "EBUSY"}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECORRUPT", 5: "ETIMEOUT", 6: "EBUSY", 7: "ECANCELED"}
 
 
 class HnswError(RuntimeError):
@@ -45,7 +45,7 @@ class IndexInfo(C.Structure):
 class SearchParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("ef", C.c_int32), ("rerank", C.c_int32), ("visited_log2", C.c_int32),
                 ("stop_threshold", C.c_float), ("stop_period", C.c_int32), ("schedule", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("check_bounds", C.c_int32)]
 
 
 class StopTrainParams(C.Structure):
@@ -66,7 +66,7 @@ class Request(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
                 ("queued", C.c_uint64), ("in_flight", C.c_uint64), ("bytes_in_use", C.c_uint64),
-                ("budget", C.c_uint64)]
+                ("budget", C.c_uint64), ("cancelled", C.c_uint64)]
 
 
 class QueryStats(C.Structure):
@@ -119,6 +119,7 @@ def lib():
             "hnsw_server_poll": (i32, [vp, u64, C.POINTER(i32)]),
             "hnsw_server_wait": (i32, [vp, u64, i32, C.POINTER(C.c_double)]),
             "hnsw_server_get_stats": (i32, [vp, C.POINTER(ServerStats)]),
+            "hnsw_server_cancel": (i32, [vp, u64]),
             "hnsw_server_destroy": (i32, [vp]),
             "hnsw_server_replay": (i32, [vp, C.POINTER(Request), vp, i64, i32, vp, vp]),
         }
@@ -324,10 +325,11 @@ class Index:
 
     def search_into(self, queries, k: int, ef: int, out_ids, out_dists, stats=None, rerank: bool = False,
                     visited_log2: int = 0, stop_threshold: float = 2.0, stop_period: int = 0,
-                    schedule: int = 0, stream=None) -> None:
+                    schedule: int = 0, stream=None, check_bounds: bool = False) -> None:
         """hnsw_search_ex into caller-owned buffers (host or device)."""
         n = int(queries.shape[0]) if queries is not None else 0
-        p = SearchParams(k, ef, int(rerank), visited_log2, stop_threshold, stop_period, schedule)
+        p = SearchParams(k, ef, int(rerank), visited_log2, stop_threshold, stop_period, schedule,
+                         int(check_bounds))
         qp, _a = _ptr(queries)
         ip, _b = _ptr(out_ids)
         dp, _c = _ptr(out_dists)
@@ -335,7 +337,8 @@ class Index:
         _check(lib().hnsw_search_ex(self.h, C.byref(p), qp, n, ip, dp, sp, _stream_ptr(stream)))
 
     def search(self, queries, k: int, ef: int, rerank: bool = False, stats: bool = False, visited_log2: int = 0,
-               stop_threshold: float = 2.0, stop_period: int = 0, schedule: int = 0, stream=None):
+               stop_threshold: float = 2.0, stop_period: int = 0, schedule: int = 0, stream=None,
+               check_bounds: bool = False):
         """Returns (ids, dists[, stats]) as arrays/tensors on the queries' device."""
         if hasattr(queries, "is_cuda") and queries.is_cuda:
             import torch
@@ -350,7 +353,8 @@ class Index:
             ds = np.empty((n, k), dtype=np.float32)
             st = np.empty((n, 4), dtype=np.uint32) if stats else None
         self.search_into(queries, k, ef, ids, ds, st, rerank=rerank, visited_log2=visited_log2,
-                         stop_threshold=stop_threshold, stop_period=stop_period, schedule=schedule, stream=stream)
+                         stop_threshold=stop_threshold, stop_period=stop_period, schedule=schedule, stream=stream,
+                         check_bounds=check_bounds)
         return (ids, ds, st) if stats else (ids, ds)
 
 
@@ -428,21 +432,30 @@ class Server:
 
     def replay(self, plan, arrival_s, timeout_ms: int = 600_000):
         """Native trace replay: plan is a list of (index_id, queries, k, ef,
-        rerank); returns (per-request (ids, dists), latency_ms, submit_s)."""
+        rerank[, stop_threshold, stop_period]); returns (per-request (ids,
+        dists), latency_ms, submit_s)."""
         n = len(plan)
         reqs = (Request * n)()
         keep = []
-        for i, (idx, q, k, ef, rr) in enumerate(plan):
+        for i, item in enumerate(plan):
+            idx, q, k, ef, rr = item[:5]
+            thr, period = (item[5], item[6]) if len(item) > 5 else (2.0, 0)
             q = np.ascontiguousarray(q, dtype=np.float32)
             ids = np.empty((q.shape[0], k), dtype=np.uint32)
             ds = np.empty((q.shape[0], k), dtype=np.float32)
-            reqs[i] = Request(idx, q.shape[0], k, ef, int(rr), 2.0, 0, q.ctypes.data, ids.ctypes.data, ds.ctypes.data)
+            reqs[i] = Request(idx, q.shape[0], k, ef, int(rr), float(thr), int(period), q.ctypes.data,
+                              ids.ctypes.data, ds.ctypes.data)
             keep.append((q, ids, ds))
         arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
         lat = np.zeros(n, dtype=np.float64)
         sub = np.zeros(n, dtype=np.float64)
         _check(lib().hnsw_server_replay(self.h, reqs, arr.ctypes.data, n, timeout_ms, lat.ctypes.data, sub.ctypes.data))
         return [(k2[1], k2[2]) for k2 in keep], lat, sub
+
+    def cancel(self, ticket: int) -> None:
+        """hnsw_server_cancel: removes a request still waiting for admission
+        (its wait then raises ECANCELED); EBUSY once it is admitted."""
+        _check(lib().hnsw_server_cancel(self.h, ticket))
 
     def poll(self, ticket: int) -> bool:
         d = C.c_int32()
