@@ -98,6 +98,11 @@ def parse():
                     help="serving mix: SIFT-shaped 1M and GloVe-shaped 1.2M indexes resident, Poisson requests")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-rate", type=float, default=20_000.0, help="mean requests per second")
+    ap.add_argument("--serving-ef-floor", action="store_true",
+                    help="serving: draw each request's ef from [max(k, floor), max(floor, 512)], floor = the "
+                         "smallest ef reaching the recall target on that index (else the mix's [k, 512])")
+    ap.add_argument("--serving-stop", action="store_true",
+                    help="serving: add a learned-stop + bf16 rerank arm (a stop network trained per index)")
     ap.add_argument("--ablation", action="store_true",
                     help="selection ablation: Alg. 3 vs Alg. 4 (with and without extendCandidates) on "
                          "clustered low-d data")
@@ -321,11 +326,12 @@ def stop_form(args, ix, X, bufs, gt, rerank, log, workload="sift", metric=0):
             if best is None or ms < best[0]:
                 best = (ms, dict(cand, recall=r), (norm, w))
     log(f"form stop: sweep {sweep}")
-    setting = None
+    setting, model = None, None
     if best is not None:
-        setting = best[1]
-        ix.set_stop_model(*best[2])
-    return {"storage": "bf16", "rerank": rerank, "sweep": sweep, "setting": setting, "training": info}
+        setting, model = best[1], best[2]
+        ix.set_stop_model(*model)
+    return {"storage": "bf16", "rerank": rerank, "sweep": sweep, "setting": setting, "training": info,
+            "model": model}
 
 
 def _search(ix, args, bufs, setting, visited_log2=0):
@@ -668,6 +674,7 @@ def main():
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved = ab / (ms / 1e3) / 1e9
+    achieved_alone = ab / (ms_alone / 1e3) / 1e9
     achieved_p = ab_p / (ms_p / 1e3) / 1e9
     traffic, sha = load_traffic(f"hnsw_search_kernel:{chosen}", sc["ef"])
     e2e_v, h2d, d2h = e2e_host(args, indexes[chosen], sc, Q, max(4, args.steps // 2))
@@ -685,7 +692,8 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f32" if fc["storage"] == "f32" else f"f32 arithmetic ({fc['storage']} storage"
+                 + (", f32 rerank)" if fc["rerank"] else ")"),
         "data": "synthetic",
         "config": {
             "workload": f"SIFT-shaped {n}-query batch over {args.n_base}x{X.shape[1]} integer-valued vectors, "
@@ -700,7 +708,9 @@ def main():
             "plain_f32": {"ef": sp["ef"], "qps": round(n * world / (ms_p / 1e3), 1),
                           "ms_per_step": round(ms_p, 4), "batch_alone_ms": round(ms_p_alone, 4),
                           "launch_ms_mean": round(launch_ms_p, 4), "recall_at_10": sp["recall"],
-                          "roofline_frac": round(achieved_p / peak, 4), "achieved_gbs": round(achieved_p, 1),
+                          "roofline_frac": round(ab_p / (ms_p_alone / 1e3) / 1e9 / peak, 4),
+                          "roofline_frac_device_throughput": round(achieved_p / peak, 4),
+                          "achieved_gbs": round(achieved_p, 1),
                           "counters": cnt_p},
             "chosen_vs_plain_qps": round(ms_p / ms, 4),
             "forms": {k2: {"setting": v["setting"], "sweep": v["sweep"], "ms_per_step": round(timing.get(k2, 0), 4),
@@ -712,13 +722,16 @@ def main():
             "build_seconds": build_s,
             "counters": cnt,
         },
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
+        "roofline": {"bound": "hbm", "achieved": round(achieved_alone, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved_alone / peak, 4), "traffic": traffic,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                      "kernel": f"hnsw_search_kernel ({chosen})", "search_cu_sha": sha,
-                     "basis": "algorithmic bytes of one launch / time per step over the timed region "
-                              "(consecutive launches overlap on the streams)",
-                     "frac_batch_alone": round(ab / (ms_alone / 1e3) / 1e9 / peak, 4)},
+                     "algorithmic_bytes_per_launch": round(ab),
+                     "basis": "algorithmic bytes of one launch / that launch's CUDA-event duration when it runs "
+                              "alone on its stream (batch_alone_ms, after an L2 flush)",
+                     "frac_device_throughput": round(achieved / peak, 4),
+                     "device_throughput_basis": "algorithmic bytes of one launch / time per step over the timed "
+                                                "region, where consecutive launches overlap on two streams"},
         "cpu_baseline": {k2: v for k2, v in cpu.items()
                          if k2 in ("value", "unit", "cores", "kind", "sample", "one_core", "cpu_model")},
         "e2e": {"value": round(e2e_v, 1), "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -1088,16 +1101,48 @@ def serving_bench(args, log):
     configurations: plain fp32, and bf16 storage with the exact fp32 rerank.
     Reports queries/s, requests/s, p50/p99 latency and recall@10 (requests
     with k >= 10) against exact k-NN."""
+    import torch
     from paper_1603_09320_gb300 import build as B
     from paper_1603_09320_gb300 import graphs, hnsw, synth
     B.build()
     sets = {}
+    floors, stop_models = {}, {}
     for name in ("sift", "glove"):
         X = synth.base(name)
         blob, bs = graphs.build_or_load(name, X.shape[0], X=X, log=log)
         Q = synth.queries(name)
-        gt = ground_truth_metric(X, Q, 10, synth.params(name)["metric"])
+        metric = synth.params(name)["metric"]
+        gt = ground_truth_metric(X, Q, 10, metric)
         sets[name] = (blob, Q, gt, bs)
+        if args.serving_ef_floor or args.serving_stop:
+            # the smallest ef reaching the recall target on this index (plain fp32, k=10, 4,096 queries)
+            ix = hnsw.Index(blob, "f32")
+            q = torch.from_numpy(Q[:4096]).cuda()
+            floors[name] = None
+            for ef in (10, 16, 24, 32, 40, 48, 50, 56, 64, 80, 96, 128, 160, 192, 256, 320, 400, 448, 498, 512, 640,
+                       800, 1000):
+                ids, _ = ix.search(q, 10, ef)
+                torch.cuda.synchronize()
+                if recall_at(ids.cpu().numpy().view(np.uint32), gt[:4096]) >= args.target_recall:
+                    floors[name] = ef
+                    break
+            ix.close()
+            log(f"serving: ef floor of {name} = {floors[name]}")
+        if args.serving_stop and floors.get(name):
+            # a stop network for the bf16 + rerank index, trained at ef_max = floor and 1.5 x floor
+            ix = hnsw.Index(blob, "bf16", keep_fp32=True)
+            nq = 10_000
+            q = torch.from_numpy(Q[:nq]).cuda()
+            bufs = (q, torch.empty((nq, 10), dtype=torch.int32, device="cuda"),
+                    torch.empty((nq, 10), dtype=torch.float32, device="cuda"),
+                    torch.empty((nq, 4), dtype=torch.int32, device="cuda"))
+            a2 = argparse.Namespace(**vars(args))
+            a2.k, a2.n_queries = 10, nq
+            a2.stop_efs = sorted({floors[name], int(floors[name] * 1.5)})
+            st = stop_form(a2, ix, X, bufs, gt[:nq], True, log, workload=name, metric=metric)
+            if st["setting"] is not None:
+                stop_models[name] = (st["model"], st["setting"])
+            ix.close()
         del X
     rng = np.random.default_rng(7)
     n_req = int(args.serving_rate * args.serving_seconds)
@@ -1108,7 +1153,11 @@ def serving_bench(args, log):
         n = min(1024, int(np.exp(rng.uniform(0, np.log(1025)))))
         s0 = int(rng.integers(0, sets[name][1].shape[0] - n + 1))
         k = int(rng.choice([1, 10, 100]))
-        ef = int(rng.integers(k, 513))
+        if args.serving_ef_floor and floors.get(name):
+            lo = max(k, floors[name])
+            ef = int(rng.integers(lo, max(lo, 512) + 1))
+        else:
+            ef = int(rng.integers(k, 513))
         plan.append((name, s0, n, k, ef))
     out = {"metric": "serving mix: p50/p99 latency and throughput", "data": "synthetic", "n_gpus": 1,
            "config": {"workload": "SIFT-shaped 1M x 128 L2 + GloVe-shaped 1.2M x 100 cosine, Poisson "
@@ -1116,35 +1165,54 @@ def serving_bench(args, log):
                                   "log-uniform, k in {1,10,100}, ef uniform [k,512], index 50/50",
                       "requests": n_req, "queries": int(sum(p[2] for p in plan)),
                       "build_seconds": {k2: v[3] for k2, v in sets.items()}}, "variants": {}}
+    if floors:
+        out["config"]["ef_floor"] = floors
     rates = sorted(set([args.serving_rate / 4, args.serving_rate / 2, args.serving_rate]))
-    for variant, (storage, keep, rerank) in {"plain_f32": ("f32", False, False),
-                                             "bf16_rerank": ("bf16", True, True)}.items():
+    variants = {"plain_f32": ("f32", False, False), "bf16_rerank": ("bf16", True, True)}
+    if len(stop_models) == len(sets):
+        variants["bf16_rerank_stop"] = ("bf16", True, True)
+        out["config"]["stop"] = {name: v[1] for name, v in stop_models.items()}
+    for variant, (storage, keep, rerank) in variants.items():
         ixs = {name: hnsw.Index(sets[name][0], storage, keep_fp32=keep) for name in sets}
+        stop_of = {}
+        if variant == "bf16_rerank_stop":
+            for name, ix in ixs.items():
+                (norm, w), setting = stop_models[name]
+                ix.set_stop_model(norm, w)
+                stop_of[name] = (setting["thr"], setting["period"])
         out["variants"][variant] = {}
         for rate in rates:
             m = int(rate * args.serving_seconds)
             arr = arrivals[:m] * (args.serving_rate / rate)  # the same requests, spread out
             sv = hnsw.Server(n_slots=16)
             ids_ = {name: sv.add_index(ix) for name, ix in ixs.items()}
-            reqs = [(ids_[name], sets[name][1][s0:s0 + n], k, ef, rerank) for (name, s0, n, k, ef) in plan[:m]]
+            reqs = [(ids_[name], sets[name][1][s0:s0 + n], k, ef, rerank) + (stop_of.get(name, (2.0, 0)))
+                    for (name, s0, n, k, ef) in plan[:m]]
             res, lat, sub = sv.replay(reqs, arr)
             st = sv.stats()
             sv.close()
             wall = float(np.max(sub + lat / 1e3))
             hits = total = 0
+            per_k = {}
             for i, (name, s0, n, k, ef) in enumerate(plan[:m]):
                 if k >= 10:
                     got = np.sort(res[i][0][:, :10].astype(np.int64), axis=1)
                     gt = np.sort(sets[name][2][s0:s0 + n], axis=1)
-                    hits += int((got[:, :, None] == gt[:, None, :]).any(axis=2).sum())
+                    h = int((got[:, :, None] == gt[:, None, :]).any(axis=2).sum())
+                    hits += h
                     total += n * 10
+                    pk = per_k.setdefault(f"k{k}_{name}", [0, 0])
+                    pk[0] += h
+                    pk[1] += n * 10
             qn = int(sum(p[2] for p in plan[:m]))
             out["variants"][variant][f"{rate:.0f}_req_per_s"] = {
                 "offered_queries_per_s": round(qn / args.serving_seconds, 1),
                 "served_queries_per_s": round(qn / wall, 1), "requests": m,
                 "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
                 "mean_ms": round(float(lat.mean()), 3), "wall_s": round(wall, 3),
-                "recall_at_10": round(hits / max(total, 1), 5), "failed": st["failed"],
+                "recall_at_10": round(hits / max(total, 1), 5),
+                "recall_at_10_by_k_and_index": {kk: round(v[0] / max(v[1], 1), 5) for kk, v in sorted(per_k.items())},
+                "failed": st["failed"],
                 "max_submit_lag_ms": round(float(np.max(sub - arr)) * 1e3, 3)}
             log(f"serving {variant} {rate:.0f}/s: {out['variants'][variant][f'{rate:.0f}_req_per_s']}")
         for ix in ixs.values():
