@@ -90,7 +90,9 @@ def parse():
     ap.add_argument("--stop-efs", type=lambda v: [int(x) for x in v.split(",")], default=[56, 64, 80])
     ap.add_argument("--stop-thresholds", type=lambda v: [float(x) for x in v.split(",")],
                     default=[0.5, 0.7, 0.8, 0.85, 0.9, 0.95, 0.98])
-    ap.add_argument("--stop-period", type=int, default=8)
+    ap.add_argument("--stop-period", type=int, default=16)
+    ap.add_argument("--stop-periods", type=lambda v: [int(x) for x in v.split(",")], default=[8, 16],
+                    help="learned stop: check periods swept (each with its own traces and network)")
     ap.add_argument("--stop-epochs", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="seconds of oracle search for the CPU baseline")
     ap.add_argument("--no-clocks", action="store_true")
@@ -302,27 +304,28 @@ def stop_form(args, ix, X, bufs, gt, rerank, log, workload="sift", metric=0):
     info = {"train_queries": int(Qt.shape[0]), "models": {}}
     sweep = []
     best = None
-    for ef_max in args.stop_efs:
-        f, tk, _, cnt, tids, _, _ = ix.search_trace(qt, k, ef_max, 128, period=args.stop_period, rerank=rerank)
+    periods = getattr(args, "stop_periods", None) or [args.stop_period]
+    for ef_max, period in [(e, pr) for pr in periods for e in args.stop_efs]:
+        f, tk, _, cnt, tids, _, _ = ix.search_trace(qt, k, ef_max, 128, period=period, rerank=rerank)
         f, tk, cnt = f.cpu().numpy(), tk.cpu().numpy().view(np.uint32), cnt.cpu().numpy()
         tids = tids.cpu().numpy().view(np.uint32)
         mask, y = stopnet.labels_from_trace(tk, cnt, tids, gt_t)
         norm, w, ls = stopnet.train_from_trace(f, mask, y, epochs=args.stop_epochs, batch=4096)
-        info["models"][ef_max] = {"samples": int(mask.sum()), "positive_frac": float(y[mask].mean()),
-                                  "loss_first": float(ls[0]), "loss_last": float(ls[-1])}
+        info["models"][f"{ef_max}/{period}"] = {"samples": int(mask.sum()), "positive_frac": float(y[mask].mean()),
+                                               "loss_first": float(ls[0]), "loss_last": float(ls[-1])}
         ix.set_stop_model(norm, w)
         for thr in args.stop_thresholds:
-            cand = {"ef": ef_max, "rerank": rerank, "thr": thr, "period": args.stop_period}
+            cand = {"ef": ef_max, "rerank": rerank, "thr": thr, "period": period}
             _search(ix, args, bufs, cand)
             torch.cuda.synchronize()
             r = recall_at(bufs[1].cpu().numpy().view(np.uint32), gt)
             sv = bufs[3].cpu().numpy().view(np.uint32)
             exp0, stopped = round(float(sv[:, 1].mean()), 2), round(float(((sv[:, 3] & 2) > 0).mean()), 3)
             if r < args.target_recall:
-                sweep.append((ef_max, thr, r, None, exp0, stopped))
+                sweep.append((ef_max, period, thr, r, None, exp0, stopped))
                 continue
             ms, _ = time_pipelined(args, ix, cand, bufs[0], 12, 2)
-            sweep.append((ef_max, thr, r, round(ms, 4), exp0, stopped))
+            sweep.append((ef_max, period, thr, r, round(ms, 4), exp0, stopped))
             if best is None or ms < best[0]:
                 best = (ms, dict(cand, recall=r), (norm, w))
     log(f"form stop: sweep {sweep}")
@@ -1129,19 +1132,43 @@ def serving_bench(args, log):
             ix.close()
             log(f"serving: ef floor of {name} = {floors[name]}")
         if args.serving_stop and floors.get(name):
-            # a stop network for the bf16 + rerank index, trained at ef_max = floor and 1.5 x floor
+            # one stop network for the bf16 + rerank index over the range of ef
+            # the requests draw from: the training queries are split over ef =
+            # floor, 128, 256 and 512 (those above the floor), their traces
+            # labelled and pooled; the threshold is the lowest of the sweep
+            # whose recall@10 reaches the target at both ends of the range
+            from paper_1603_09320_gb300 import stopnet
             ix = hnsw.Index(blob, "bf16", keep_fp32=True)
-            nq = 10_000
-            q = torch.from_numpy(Q[:nq]).cuda()
-            bufs = (q, torch.empty((nq, 10), dtype=torch.int32, device="cuda"),
-                    torch.empty((nq, 10), dtype=torch.float32, device="cuda"),
-                    torch.empty((nq, 4), dtype=torch.int32, device="cuda"))
-            a2 = argparse.Namespace(**vars(args))
-            a2.k, a2.n_queries = 10, nq
-            a2.stop_efs = sorted({floors[name], int(floors[name] * 1.5)})
-            st = stop_form(a2, ix, X, bufs, gt[:nq], True, log, workload=name, metric=metric)
-            if st["setting"] is not None:
-                stop_models[name] = (st["model"], st["setting"])
+            Qt = synth.queries(name, args.train_queries, training=True)
+            gt_t = ground_truth_metric(X, Qt, 10, metric)
+            efs = sorted({floors[name]} | {e for e in (128, 256, 512) if e > floors[name]})
+            fs, ys = [], []
+            for j, ef in enumerate(efs):
+                lo, hi = j * len(Qt) // len(efs), (j + 1) * len(Qt) // len(efs)
+                f, tk, _, cnt, tids, _, _ = ix.search_trace(torch.from_numpy(Qt[lo:hi]).cuda(), 10, ef, 128,
+                                                             period=args.stop_period, rerank=True)
+                mask, y = stopnet.labels_from_trace(tk.cpu().numpy().view(np.uint32), cnt.cpu().numpy(),
+                                                    tids.cpu().numpy().view(np.uint32), gt_t[lo:hi])
+                fs.append(f.cpu().numpy()[mask])
+                ys.append(y[mask])
+            Xt = torch.as_tensor(np.ascontiguousarray(np.concatenate(fs), dtype=np.float32)).cuda()
+            Yt = torch.as_tensor(np.ascontiguousarray(np.concatenate(ys), dtype=np.float32)).cuda()
+            norm, w, _ = hnsw.stop_train(Xt, Yt, stopnet.init_weights(0), epochs=args.stop_epochs, batch=4096)
+            ix.set_stop_model(norm, w)
+            q = torch.from_numpy(Q[:10_000]).cuda()
+            chosen = None
+            for thr in sorted(args.stop_thresholds):
+                ok = True
+                for ef in (efs[0], efs[-1]):
+                    ids, _ = ix.search(q, 10, ef, rerank=True, stop_threshold=thr, stop_period=args.stop_period)
+                    torch.cuda.synchronize()
+                    ok = ok and recall_at(ids.cpu().numpy().view(np.uint32), gt[:10_000]) >= args.target_recall
+                if ok:
+                    chosen = thr
+                    break
+            log(f"serving: stop network of {name} trained over ef {efs}, threshold {chosen}")
+            if chosen is not None:
+                stop_models[name] = ((norm, w), {"thr": chosen, "period": args.stop_period, "trained_efs": efs})
             ix.close()
         del X
     rng = np.random.default_rng(7)

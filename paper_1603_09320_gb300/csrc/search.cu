@@ -38,10 +38,13 @@
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 
 #include "common.hpp"
 #include "index.cuh"
@@ -58,23 +61,12 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 // one after another.  HNSW_PREFETCH_NEXT: while an element is expanded, the
 // neighbour row of the next unexpanded entry of W is loaded speculatively;
 // it is the next element to expand unless the current batch inserts a better
-// one.  HNSW_MIN_BLOCKS: minimum resident blocks per SM for the register
-// allocation of the search kernel (0: let ptxas choose).
+// one.
 #ifndef HNSW_PREFETCH_ROWS
 #define HNSW_PREFETCH_ROWS 0
 #endif
 #ifndef HNSW_PREFETCH_NEXT
 #define HNSW_PREFETCH_NEXT 1
-#endif
-#ifndef HNSW_MIN_BLOCKS
-#define HNSW_MIN_BLOCKS 0
-#endif
-// HNSW_STOP_GLOBAL: STOP launches read the stop network from global memory
-// (10.3 KB, held in L1 by every SM that uses it) and run the plain search's
-// 128-thread blocks, so that consecutive launches still share the SMs; 0: one
-// shared-memory copy of the network per block and large blocks
-#ifndef HNSW_STOP_GLOBAL
-#define HNSW_STOP_GLOBAL 1
 #endif
 // HNSW_STOP_SKIP_IMPROVING: outside trace recording, a due check is put off
 // while the expansion just done changed the K nearest of W (the search is
@@ -100,13 +92,6 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 #ifndef HNSW_B16_U
 #define HNSW_B16_U 2
 #endif
-// HNSW_PAIRED_FMA: distances with the paired fp32 operations of sm_100+
-// (two coordinates per fused multiply-add; two partial sums per row, added
-// at the end); for squared L2 the query is held negated, x + (-q) being
-// exactly -(q - x)
-#ifndef HNSW_PAIRED_FMA
-#define HNSW_PAIRED_FMA 0
-#endif
 // HNSW_MIXED_SUB: for bf16 / f16 rows and squared L2, x - q in one
 // mixed-precision subtraction per coordinate (the 16-bit x taken as it is
 // stored, q in fp32, the difference rounded once to fp32: the same value as
@@ -125,11 +110,6 @@ __device__ __forceinline__ void sub_halves(uint32_t w, float q0, float q1, float
         asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n sub.rn.f32.f16 %0, l, %3;\n sub.rn.f32.f16 %1, h, %4;\n}"
             : "=f"(t0), "=f"(t1) : "r"(w), "f"(q0), "f"(q1));
 }
-#if HNSW_MIN_BLOCKS > 0
-#define HNSW_SEARCH_BOUNDS __launch_bounds__(128, HNSW_MIN_BLOCKS)
-#else
-#define HNSW_SEARCH_BOUNDS __launch_bounds__(128)
-#endif
 
 struct SearchArgs {
     DevIndex ix;
@@ -140,6 +120,12 @@ struct SearchArgs {
     int efcap;      // power of two >= efp
     int hlog;       // log2 visited slots
     int warp_smem;  // bytes of shared memory per warp
+    // per-warp layout: W, the visited set, ids, dst, nbuf (kMaxDeg entries
+    // each) and aux (64 bytes) at fixed places, then at these byte offsets
+    // from the warp's region: ck and lbs (present only when merge_batch or a
+    // stop check may use them) and qs (the rerank's copy of q, in the
+    // visited set's bytes when they suffice: it is filled after the search)
+    int off_ck, off_lbs, off_qs;
     int rerank;
     uint32_t* out_ids;
     float* out_dists;
@@ -298,16 +284,15 @@ struct Dist {
     static constexpr int RPR = TEAMS * U;  // rows per round
     static constexpr bool MIXED = HNSW_MIXED_SUB && (ST == HNSW_BF16 || ST == HNSW_F16);
 
-    __device__ static void load_q(const float* qp, uint32_t d, float (&qr)[QF], int lane, int metric) {
+    __device__ static void load_q(const float* qp, uint32_t d, float (&qr)[QF], int lane) {
         const int tl = lane % TEAM;
-        const float sg = (HNSW_PAIRED_FMA && !MIXED && metric == HNSW_L2SQ) ? -1.0f : 1.0f;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             const int ch = tl + c * TEAM;
 #pragma unroll
             for (int j = 0; j < CPC; ++j) {
                 const uint32_t co = uint32_t(ch * CPC + j);
-                qr[c * CPC + j] = co < d ? sg * qp[co] : 0.0f;
+                qr[c * CPC + j] = co < d ? qp[co] : 0.0f;
             }
         }
     }
@@ -340,9 +325,6 @@ struct Dist {
             for (int u = 0; u < U; ++u) {
                 float acc = 0.0f;
                 if (MIXED && ix.metric == HNSW_L2SQ) {
-#if HNSW_PAIRED_FMA
-                    float2 acc2 = make_float2(0.0f, 0.0f);
-#endif
 #pragma unroll
                     for (int c = 0; c < CPL; ++c) {
                         const uint32_t w[4] = {v[u][c].x, v[u][c].y, v[u][c].z, v[u][c].w};
@@ -350,40 +332,11 @@ struct Dist {
                         for (int i = 0; i < 4; ++i) {
                             float t0, t1;
                             sub_halves<ST>(w[i], qr[c * CPC + 2 * i], qr[c * CPC + 2 * i + 1], t0, t1);
-#if HNSW_PAIRED_FMA
-                            const float2 t = make_float2(t0, t1);
-                            acc2 = __ffma2_rn(t, t, acc2);
-#else
                             acc = fmaf(t0, t0, acc);
                             acc = fmaf(t1, t1, acc);
-#endif
                         }
                     }
-#if HNSW_PAIRED_FMA
-                    acc = acc2.x + acc2.y;
-#endif
                 } else {
-#if HNSW_PAIRED_FMA
-                float2 acc2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-                for (int c = 0; c < CPL; ++c) {
-                    float x[CPC];
-                    Store<ST>::decode(v[u][c], x);
-#pragma unroll
-                    for (int j = 0; j < CPC; j += 2) {
-                        float2 x2 = make_float2(x[j], x[j + 1]);
-                        if (ST == HNSW_FP8E4M3) x2 = make_float2(x2.x * sc[u], x2.y * sc[u]);
-                        const float2 q2 = make_float2(qr[c * CPC + j], qr[c * CPC + j + 1]);
-                        if (ix.metric == HNSW_L2SQ) {
-                            const float2 t = __fadd2_rn(x2, q2);
-                            acc2 = __ffma2_rn(t, t, acc2);
-                        } else {
-                            acc2 = __ffma2_rn(q2, x2, acc2);
-                        }
-                    }
-                }
-                acc = acc2.x + acc2.y;
-#else
 #pragma unroll
                 for (int c = 0; c < CPL; ++c) {
                     float x[CPC];
@@ -403,7 +356,6 @@ struct Dist {
                         }
                     }
                 }
-#endif
                 }
 #pragma unroll
                 for (int o = TEAM / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
@@ -660,7 +612,6 @@ __device__ void warp_sort(uint64_t* a, int n, int lane) {
         }
 }
 
-__device__ __forceinline__ uint32_t ix_row32(const SearchArgs& a) { return a.ix.row_chunks32 * 4; }
 
 // ---- the kernel -------------------------------------------------------------
 // STOP: the build with learned-stop checks and trace recording (the plain
@@ -683,30 +634,29 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 #pragma unroll
     for (int i = 1; i < kStopIn; ++i) fv = lane == i ? f[i] : fv;
     if (lane < kStopIn) aux[4 + lane] = fv;
-    return model ? stop_logit<HNSW_STOP_GLOBAL != 0>(model, f, hs, lane) : 0.0f;
+    return model ? stop_logit<true>(model, f, hs, lane) : 0.0f;
 }
 
-// STOP builds copy the stop network to shared memory once per block, so they
-// run large blocks: one block of 32 warps per SM at 64 registers, or for the
-// fp32 128-d variant (which spills below about 80 registers) 3 blocks of 8
-// warps.
-template <int ST, int CPL>
-constexpr bool stop_wide_regs() { return ST == HNSW_F32 && CPL == 4; }
-
-// Resident 128-thread blocks per SM that each plain instantiation's register
-// budget is set for (65,536 registers / (128 x blocks) per thread): 8 (64
-// registers) where the kernel fits without spilling, fewer where its rows in
-// flight need more (fp32 128-d: 72; fp8 with 8 rows per team: about 96; f16
-// with 4 rows per team: about 80).  Without an explicit count the compiler
-// chose budgets that spilled.
-template <int ST, int CPL, int U>
-constexpr int plain_min_blocks() {
-    return (ST == HNSW_F32 && CPL == 4) ? 7 : (ST == HNSW_FP8E4M3 && U == 8) ? 5 : (ST == HNSW_F16 && U == 4) ? 6 : 8;
-}
-
-#ifndef HNSW_STOP_THREADS
-#define HNSW_STOP_THREADS 1024
+// Register budget of each instantiation (per thread).  56 -- 9 blocks of 128
+// threads resident per SM, 36 warps -- where the kernel fits in it without
+// spilling (full bf16 rows of 2 chunks per lane, the 2-lane teams of low-d
+// rows); 64 (8 blocks) for the other narrow ones; more where the rows in
+// flight need them (fp32 128-d: 72, with the stop checks 80; fp8 with 8 rows
+// per team: 96; f16 with 4 rows per team: 80).  Without an explicit budget
+// the compiler chose budgets that spilled.  Blocks of up to 256 threads are
+// allowed so that large per-warp state (wide beams) can be packed into the
+// shared memory of an SM (see the launch).
+#ifndef HNSW_NARROW_REGS
+#define HNSW_NARROW_REGS 56
 #endif
+template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP, bool CHECK>
+constexpr int search_max_regs() {
+    return (ST == HNSW_F32 && CPL == 4) ? (STOP ? 80 : 72)
+         : (ST == HNSW_FP8E4M3 && U == 8) ? 96
+         : (ST == HNSW_F16 && U == 4) ? 80
+         : (!STOP && !CHECK && ((ST == HNSW_BF16 && TEAM == 8 && CPL == 2 && FULL) || TEAM == 2)) ? HNSW_NARROW_REGS
+                                                                                      : 64;
+}
 
 // CHECK: the bounds-checked build (hnsw_search_params.check_bounds): every
 // element id read from the graph is tested against N and every upper-row
@@ -714,11 +664,7 @@ constexpr int plain_min_blocks() {
 // one sets stats flag bit 2 and leaves its search (its results are what W
 // holds), with no device fault and no trap.
 template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP, bool CHECK = false>
-__global__ void __launch_bounds__(
-    (STOP && !HNSW_STOP_GLOBAL) ? (stop_wide_regs<ST, CPL>() ? 256 : HNSW_STOP_THREADS) : 128,
-    STOP ? (HNSW_STOP_GLOBAL ? (stop_wide_regs<ST, CPL>() ? 6 : plain_min_blocks<ST, CPL, U>())
-                             : (stop_wide_regs<ST, CPL>() ? 3 : 1))
-         : plain_min_blocks<ST, CPL, U>())
+__global__ void __launch_bounds__(256) __maxnreg__((search_max_regs<ST, TEAM, CPL, U, FULL, STOP, CHECK>()))
     hnsw_search_kernel(const SearchArgs a) {
     using D = Dist<ST, TEAM, CPL, U, FULL>;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -728,10 +674,7 @@ __global__ void __launch_bounds__(
     uint32_t* H = reinterpret_cast<uint32_t*>(wbase + a.efcap * 8);
     uint32_t* ids = H + (1 << a.hlog);
     float* dst = reinterpret_cast<float*>(ids + kMaxDeg);
-    uint64_t* ck = reinterpret_cast<uint64_t*>(dst + kMaxDeg);
-    uint32_t* lbs = reinterpret_cast<uint32_t*>(ck + kMaxDeg);
-    float* qs = reinterpret_cast<float*>(lbs + kMaxDeg);
-    uint32_t* nbuf = reinterpret_cast<uint32_t*>(qs + ix_row32(a));  // staged neighbour row (16-byte aligned)
+    uint32_t* nbuf = reinterpret_cast<uint32_t*>(dst + kMaxDeg);  // staged neighbour row (16-byte aligned)
     // per-query scalars read only at stop checks (kept out of registers):
     // 1/d1, log1p(d1), n_eval at layer 0 entry, checks recorded; [4..9] the
     // features of the last check
@@ -739,14 +682,6 @@ __global__ void __launch_bounds__(
     uint32_t* n_checks = reinterpret_cast<uint32_t*>(aux + 3);
     const DevIndex& ix = a.ix;
     const int hsz = 1 << a.hlog;
-    // the stop network, one copy per block after the warps' regions (its
-    // address is recomputed at each check rather than held in registers)
-    if (STOP && !HNSW_STOP_GLOBAL && a.stop) {
-        uint4* d4 = reinterpret_cast<uint4*>(smem + (blockDim.x >> 5) * a.warp_smem);
-        const uint4* src = reinterpret_cast<const uint4*>(a.stop);
-        for (int i = threadIdx.x; i < int(sizeof(StopDev) / 16); i += blockDim.x) d4[i] = src[i];
-        __syncthreads();
-    }
     for (;;) {
         uint32_t qi = 0;
         if (lane == 0) qi = atomicAdd(a.work, 1u);
@@ -762,9 +697,7 @@ __global__ void __launch_bounds__(
             efq = max(int(v & 0xffffu), int(v >> 16));
         }
         float qr[D::QF];
-        D::load_q(qp, ix.d, qr, lane, ix.metric);
-        if (a.rerank)
-            for (uint32_t i = lane; i < ix.row_chunks32 * 4; i += 32) qs[i] = i < ix.d ? qp[i] : 0.0f;
+        D::load_q(qp, ix.d, qr, lane);
         for (int i = lane; i < (hsz >> 2); i += 32)
             reinterpret_cast<uint4*>(H)[i] = make_uint4(kNone, kNone, kNone, kNone);
         uint32_t n_eval = 0, n_exp0 = 0, n_stepU = 0, flags = 0;
@@ -786,10 +719,10 @@ __global__ void __launch_bounds__(
             __syncwarp();
             cur = mkkey(dst[0], ix.ep);
             n_eval = 1;
+            uint32_t cur_uo = ix.maxlevel >= 1 ? __ldg(ix.upoff + key_id(cur)) : kNone;  // cur's first upper row
             for (int lc = ix.maxlevel; lc >= 1 && !bad; --lc) {
                 for (;;) {
-                    const uint32_t c = key_id(cur);
-                    const uint64_t row = uint64_t(__ldg(ix.upoff + c)) + uint64_t(lc - 1);
+                    const uint64_t row = uint64_t(cur_uo) + uint64_t(lc - 1);
                     if (CHECK && !(row < ix.urows)) {  // c absent from layer lc, or a bad offset
                         bad = true;
                         break;
@@ -822,6 +755,7 @@ __global__ void __launch_bounds__(
                     kb = warp_min_u64(kb);
                     if ((kb >> 1) < (cur >> 1)) {
                         cur = kb;
+                        cur_uo = __ldg(ix.upoff + key_id(kb));
                     } else {
                         break;
                     }
@@ -859,12 +793,20 @@ __global__ void __launch_bounds__(
             for (;;) {
                 if (CHECK && bad) break;  // the descent met a bad id or row: W holds its last element
                 int p = -1;
+                // the window of W where p was found: its unexpanded entries
+                // (bit per lane) and this lane's entry, for the next one after p
+                unsigned win_m = 0u;
+                uint32_t win_id = 0u;
                 for (int s = scan; s < size; s += 32) {
                     const int i = s + lane;
-                    const bool un = i < size && !(W[i] & 1ull);
+                    const uint64_t wk = i < size ? W[i] : 1ull;
+                    const bool un = !(wk & 1ull);
                     const unsigned m = __ballot_sync(kFull, un);
                     if (m) {
-                        p = s + __ffs(m) - 1;
+                        const int b = __ffs(m) - 1;
+                        p = s + b;
+                        win_m = b < 31 ? (m & (~0u << (b + 1))) : 0u;
+                        win_id = key_id(wk);
                         break;
                     }
                 }
@@ -903,12 +845,18 @@ __global__ void __launch_bounds__(
                 // batch inserts a better element: stage its neighbour row now
                 nxt_id = kNone;
                 {
-                    const int i = p + 1 + lane;
-                    const bool un = i < size && !(W[i] & 1ull);
-                    const unsigned m = __ballot_sync(kFull, un);
+                    // within the window of p when it holds one, else the 32
+                    // entries after p
+                    unsigned m = win_m;
+                    uint32_t id = win_id;
+                    if (!m) {
+                        const int i = p + 1 + lane;
+                        const bool un = i < size && !(W[i] & 1ull);
+                        m = __ballot_sync(kFull, un);
+                        id = un ? key_id(W[i]) : 0u;
+                    }
                     if (m) {
-                        const int src = __ffs(m) - 1;
-                        nxt_id = __shfl_sync(kFull, un ? key_id(W[i]) : 0u, src);
+                        nxt_id = __shfl_sync(kFull, id, __ffs(m) - 1);
                         const uint32_t* np = ix.nbr0 + uint64_t(nxt_id) * ix.s0;
                         if (lane * 4 < deg) cp_async16(nbuf + lane * 4, np + lane * 4);
                         cp_async_commit();
@@ -946,7 +894,9 @@ __global__ void __launch_bounds__(
                     n_eval += n;
                     first_new = (a.efcap <= 64 && n <= 32)
                                     ? merge_small(W, size, efq, ids, dst, n, lane)
-                                    : merge_batch(W, size, efq, ids, dst, n, ck, lbs, lane);
+                                    : merge_batch(W, size, efq, ids, dst, n,
+                                                  reinterpret_cast<uint64_t*>(wbase + a.off_ck),
+                                                  reinterpret_cast<uint32_t*>(wbase + a.off_lbs), lane);
                 }
                 scan = min(p + 1, first_new);
                 if (STOP && a.stop_period > 0) {
@@ -964,12 +914,9 @@ __global__ void __launch_bounds__(
                     if (check) stale_cd |= uint32_t(a.stop_period);
                     if (size >= kq && check) {
                         __syncwarp();
-                        const StopDev* model =
-                            !a.stop ? nullptr
-                            : HNSW_STOP_GLOBAL ? a.stop
-                                               : reinterpret_cast<const StopDev*>(smem + (blockDim.x >> 5) * a.warp_smem);
+                        const StopDev* model = a.stop;  // global memory, read through L1
                         const float logit = stop_check(model, W, size, kq, aux, n_eval - __float_as_uint(aux[2]),
-                                                       stale_cd >> 16, reinterpret_cast<float*>(ck), lane);
+                                                       stale_cd >> 16, reinterpret_cast<float*>(wbase + a.off_ck), lane);
                         if (a.tr_count) {
                             __syncwarp();
                             const uint32_t c = *n_checks;
@@ -993,6 +940,11 @@ __global__ void __launch_bounds__(
         }
         // results (the K nearest of W, Alg. 5)
         if (a.rerank && size > 0) {
+            float* qs = reinterpret_cast<float*>(wbase + a.off_qs);
+            const float* qrow = a.q + uint64_t(qi) * ix.d;  // re-derived: keeps qp out of the loop's registers
+            __syncwarp();
+            for (uint32_t i = lane; i < ix.row_chunks32 * 4; i += 32) qs[i] = i < ix.d ? qrow[i] : 0.0f;
+            __syncwarp();
             for (int b = 0; b < size; b += kMaxDeg) {
                 const int nb = min(kMaxDeg, size - b);
                 for (int i = lane; i < nb; i += 32) ids[i] = key_id(W[b + i]);
@@ -1148,6 +1100,50 @@ int ceil_log2(uint64_t x) {
     return r;
 }
 
+// Warps per block (1..8) that put the most warps of kernel fn on an SM
+// given `warp_smem` bytes of shared memory per warp (the fewest warps per
+// block among equals: finer-grained blocks), and the blocks per SM then.
+// Small per-warp state is bound by registers (4-warp blocks); a wide beam's
+// state is bound by shared memory, where the block size decides how much of
+// an SM's 228 KB the blocks fill.  Cached per (device, kernel, size).
+bool block_choice(KernelFn fn, size_t warp_smem, int& warps, int& per_sm) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, size_t>, std::pair<int, int>> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, reinterpret_cast<const void*>(fn), warp_smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            warps = it->second.first;
+            per_sm = it->second.second;
+            return true;
+        }
+    }
+    int best = 0;
+    warps = 0;
+    per_sm = 0;
+    for (int w : {4, 5, 6, 7, 8, 3, 2, 1}) {
+        const size_t sm = size_t(w) * warp_smem;
+        if (sm > 227 * 1024) continue;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, w * 32, sm) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (b * w > best) {
+            best = b * w;
+            warps = w;
+            per_sm = b;
+        }
+    }
+    if (best == 0) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = {warps, per_sm};
+    return true;
+}
+
 }  // namespace
 
 int auto_visited_log2(int efp) {
@@ -1201,31 +1197,39 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
         a.tr_count = stop->tr_count;
         a.tr_max = stop->tr_max;
     }
-    const size_t per_warp = size_t(a.efcap) * 8 + (size_t(1) << a.hlog) * 4 + kMaxDeg * (4 + 4 + 8 + 4) +
-                            size_t(D.row_chunks32) * 16 + kMaxDeg * 4 + 64;
-    a.warp_smem = int((per_warp + 15) & ~size_t(15));
     const bool stop_build = stop != nullptr && stop->period > 0;
-    const size_t model_smem = (!HNSW_STOP_GLOBAL && stop_build && stop->stop) ? sizeof(StopDev) : 0;
-    int warps = 4;
-    if (stop_build && !HNSW_STOP_GLOBAL) {
-        cudaFuncAttributes fa{};
-        cudaError_t e = cudaFuncGetAttributes(&fa, kc.fn);
-        if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("search: attributes: ") + cudaGetErrorString(e));
-        warps = fa.maxThreadsPerBlock / 32;
-        while (warps > 1 && size_t(warps) * a.warp_smem + model_smem > 227 * 1024) --warps;
+    // per-warp layout (every piece a multiple of 16 bytes)
+    const size_t hbytes = (size_t(1) << a.hlog) * 4, row32 = size_t(D.row_chunks32) * 16;
+    size_t per_warp = size_t(a.efcap) * 8 + hbytes + kMaxDeg * 12 + 64;
+    // merge_batch (W above 64 entries, or a neighbour batch above 32) and
+    // the stop check's scratch use ck and lbs
+    if (stop_build || a.efcap > 64 || D.s0 > 32) {
+        a.off_ck = int(per_warp);
+        a.off_lbs = int(per_warp + kMaxDeg * 8);
+        per_warp += kMaxDeg * 12;
+    } else {
+        a.off_ck = a.off_lbs = 0;
     }
-    while (warps > 1 && size_t(warps) * a.warp_smem + model_smem > 227 * 1024) warps >>= 1;
-    const size_t smem = size_t(warps) * a.warp_smem + model_smem;
-    if (smem > 227 * 1024) return fail(HNSW_EINVAL, "search: ef/visited set too large for shared memory");
-    int dev = 0, sms = 0, per_sm = 0;
+    if (!p.rerank || hbytes >= row32) {
+        a.off_qs = a.efcap * 8;  // the visited set's bytes
+    } else {
+        a.off_qs = int(per_warp);
+        per_warp += row32;
+    }
+    a.warp_smem = int(per_warp);
+    if (size_t(a.warp_smem) > 227 * 1024)
+        return fail(HNSW_EINVAL, "search: ef/visited set too large for shared memory");
+    int dev = 0, sms = 0, per_sm = 0, warps = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     {
-        const hnsw_status st = raise_smem_limit(reinterpret_cast<const void*>(kc.fn), smem, "search");
+        const size_t most = std::min<size_t>(227 * 1024, size_t(8) * a.warp_smem);
+        const hnsw_status st = raise_smem_limit(reinterpret_cast<const void*>(kc.fn), most, "search");
         if (st != HNSW_OK) return st;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc.fn, warps * 32, smem);
-    if (per_sm < 1) per_sm = 1;
+    if (!block_choice(kc.fn, size_t(a.warp_smem), warps, per_sm))
+        return fail(HNSW_ECUDA, "search: occupancy query failed");
+    const size_t smem = size_t(warps) * a.warp_smem;
     const uint64_t need = (uint64_t(n) + warps - 1) / warps;
     const uint64_t cap = uint64_t(per_sm) * uint64_t(sms);
     const unsigned grid = unsigned(need < cap ? need : cap);

@@ -13,7 +13,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <cstring>
 
 namespace hnswgb {
 
@@ -38,34 +37,15 @@ struct StopDev {
 };
 static_assert(sizeof(StopDev) % 16 == 0, "StopDev is copied in 16-byte words");
 
-// Loads of the network's weights.  From global memory (GLOBAL) they are
-// marked L1::evict_last (HNSW_STOP_EVICT_LAST), so that the 10 KB network
-// stays in an SM's L1 while the search streams vector rows through it; from
-// shared memory they are plain loads.
-#ifndef HNSW_STOP_EVICT_LAST
-#define HNSW_STOP_EVICT_LAST 1
-#endif
+// Loads of the network's weights: read-only global loads (GLOBAL) or plain
+// shared-memory loads.
 template <bool GLOBAL>
 __device__ __forceinline__ float ldw(const float* p) {
-    if (GLOBAL && HNSW_STOP_EVICT_LAST) {
-        float v;
-        asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
-        return v;
-    }
-    if (GLOBAL) return __ldg(p);
-    return *p;
+    return GLOBAL ? __ldg(p) : *p;
 }
 template <bool GLOBAL>
 __device__ __forceinline__ __half2 ldw(const __half2* p) {
-    if (GLOBAL && HNSW_STOP_EVICT_LAST) {
-        uint32_t v;
-        asm("ld.global.nc.L1::evict_last.b32 %0, [%1];" : "=r"(v) : "l"(p));
-        __half2 h;
-        memcpy(&h, &v, 4);
-        return h;
-    }
-    if (GLOBAL) return __ldg(p);
-    return *p;
+    return GLOBAL ? __ldg(p) : *p;
 }
 
 // Logit of the network for features f (identical in every lane), computed by
