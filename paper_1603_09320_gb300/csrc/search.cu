@@ -641,7 +641,7 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 // threads resident per SM, 36 warps -- where the kernel fits in it without
 // spilling (full bf16 rows of 2 chunks per lane, the 2-lane teams of low-d
 // rows); 64 (8 blocks) for the other narrow ones; more where the rows in
-// flight need them (fp32 128-d: 72, with the stop checks 80; fp8 with 8 rows
+// flight need them (fp32 128-d: 72, with the stop or bounds checks 80; fp8 with 8 rows
 // per team: 96; f16 with 4 rows per team: 80).  Without an explicit budget
 // the compiler chose budgets that spilled.  Blocks of up to 256 threads are
 // allowed so that large per-warp state (wide beams) can be packed into the
@@ -651,7 +651,7 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 #endif
 template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP, bool CHECK>
 constexpr int search_max_regs() {
-    return (ST == HNSW_F32 && CPL == 4) ? (STOP ? 80 : 72)
+    return (ST == HNSW_F32 && CPL == 4) ? ((STOP || CHECK) ? 80 : 72)
          : (ST == HNSW_FP8E4M3 && U == 8) ? 96
          : (ST == HNSW_F16 && U == 4) ? 80
          : (!STOP && !CHECK && ((ST == HNSW_BF16 && TEAM == 8 && CPL == 2 && FULL) || TEAM == 2)) ? HNSW_NARROW_REGS
