@@ -11,12 +11,13 @@
 //   2. SEARCH-LAYER(q, ep, ef', 0) (Alg. 2, ef' = max(ef, K)) as ONE list W in
 //      shared memory, sorted by key and capped at ef', with an "expanded" bit
 //      per entry instead of the two priority queues: under key order the
-//      unextracted candidates that can still be expanded before the break of
-//      Alg. 2's stop test are exactly the unexpanded entries of W, so "extract the
-//      nearest of C" is "take the first unexpanded entry" and the loop ends
-//      when none is left.  All unvisited neighbours of the expanded element
-//      are scored together and merged at once; sequential insertion by lines
-//      12-17 leaves the same top-ef' of the union.
+//      unextracted candidates that can still be expanded before Alg. 2's
+//      stop test fires are exactly the unexpanded entries of W, so "extract
+//      the nearest of C" is "take the first unexpanded entry" and the loop
+//      ends when none is left.  All unvisited neighbours of the expanded
+//      element are scored together and merged at once; inserting them one at
+//      a time by Alg. 2's admission and eviction leaves the same top-ef' of
+//      the union.
 //   3. the K first entries of W (Alg. 5's result), or, with rerank, the K best
 //      of W by exact fp32 distance recomputed from the fp32 copy.
 //
