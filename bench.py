@@ -23,6 +23,7 @@ gathers over 2 GB.  One batch alone, after an L2 flush, is timed beside it.
 from __future__ import annotations
 
 import argparse
+import re
 import hashlib
 import json
 import os
@@ -483,10 +484,19 @@ def e2e_host(args, ix, setting, Q, steps):
     return nt * per * n / dt, int(qh.numel() * 4), int(ih.numel() * 4 + dh.numel() * 4)
 
 
+def kernel_source_sha():
+    """Hash of search.cu's code with comments and blank space removed, so that
+    counters taken on a kernel stay matched to it across comment edits."""
+    src = open(os.path.join(ROOT, "paper_1603_09320_gb300", "csrc", "search.cu")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = " ".join(src.split())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def load_traffic(kernel_tag, ef):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    src = open(os.path.join(ROOT, "paper_1603_09320_gb300", "csrc", "search.cu"), "rb").read()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    sha = kernel_source_sha()
     if not os.path.exists(path):
         return None, sha
     try:

@@ -111,6 +111,24 @@ def test_clock_samples_are_summarised(tmp_path):
 def test_traffic_counters_only_for_the_same_kernel_source():
     traffic, sha = bench.load_traffic("no-such-kernel", 50)
     assert traffic is None and len(sha) == 16
+    # the committed counters belong to this kernel's code, at the bench's ef
+    traffic, sha = bench.load_traffic("hnsw_search_kernel:bf16r", 50)
+    assert traffic is not None and traffic > 1e9
+    assert bench.load_traffic("hnsw_search_kernel:bf16r", 64)[0] is None
+
+
+def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
+    # a comment edit keeps the hash; a code edit changes it
+    src = open(os.path.join(ROOT, "paper_1603_09320_gb300", "csrc", "search.cu")).read()
+    d = tmp_path / "paper_1603_09320_gb300" / "csrc"
+    d.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (d / "search.cu").write_text(src)
+    h0 = bench.kernel_source_sha()
+    (d / "search.cu").write_text(src.replace("// search.cu --", "// search.cu (edited comment) --", 1) + "\n// x\n")
+    assert bench.kernel_source_sha() == h0
+    (d / "search.cu").write_text(src.replace("constexpr int kMaxDeg = 64;", "constexpr int kMaxDeg = 32;", 1))
+    assert bench.kernel_source_sha() != h0
 
 
 def test_reference_arm_prints_the_contract_line():
