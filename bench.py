@@ -118,6 +118,9 @@ def parse():
     ap.add_argument("--insert", action="store_true",
                     help="incremental insertion: the last 10% of the bench vectors inserted into a resident index "
                          "while searches run")
+    ap.add_argument("--sharded", action="store_true",
+                    help="data-sharded search: each rank holds the graph of one contiguous shard of the base set, "
+                         "every rank searches every query, the ranks' answers are all-gathered and merged")
     ap.add_argument("--build-compare", action="store_true",
                     help="graph construction: hnsw_build_gpu against the host builder on the bench workload")
     ap.add_argument("--profile-form", default=None,
@@ -610,6 +613,8 @@ def main():
         return angular_bench(args, log)
     if args.lowd:
         return lowd_bench(args, log)
+    if args.sharded:
+        return sharded_bench(args, rank, world, local, log)
 
     import torch
     torch.cuda.set_device(local)
@@ -754,6 +759,92 @@ def main():
     out["cpu_baseline"]["recall_at_10"] = cpu["recall"]
     out["cpu_baseline"]["oracle_n_dist_mean"] = cpu["n_dist_mean"]
     print(json.dumps(out), flush=True)
+
+
+def sharded_bench(args, rank, world, local, log):
+    """Data-sharded search on the SIFT-shaped workload: rank r holds the
+    graph of base elements shard_range(N, r, world), built by the host
+    builder over that range alone, bf16 storage with the fp32 rerank; every
+    rank searches each 10,000-query batch; the ranks' k nearest are
+    all-gathered (NCCL) and merged on every rank by hnsw_merge_topk.  ef is
+    the smallest of the sweep whose merged answers reach the recall target;
+    value = queries answered / the slowest rank's time (strong scaling: the
+    job answers each query once, each rank searches 1/world of the data)."""
+    import socket
+
+    import torch
+    import torch.distributed as dist
+    from paper_1603_09320_gb300 import build as B
+    from paper_1603_09320_gb300 import graphs, hnsw, sharded, synth
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.init_process_group("nccl")
+        dist.barrier()
+    else:
+        with socket.socket() as so:
+            so.bind(("127.0.0.1", 0))
+            port = so.getsockname()[1]
+        dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    hnsw.lib()
+    X, Q, u = workload(args)
+    N = X.shape[0]
+    lo, hi = sharded.shard_range(N, rank, world)
+    p = synth.params("sift")
+    t0 = time.perf_counter()
+    if world == 1:
+        blob, _ = graphs.build_or_load("sift", N, threads=args.threads, X=X, log=log)
+    else:
+        blob = hnsw.build_graph(X[lo:hi], u[lo:hi], M=p["M"], Mmax=p["Mmax"], Mmax0=p["Mmax0"],
+                                ef_construction=p["efC"], n_threads=args.threads)
+    t_build = time.perf_counter() - t0
+    gt = ground_truth(X, Q, args.k, torch.device("cuda", local)) if rank == 0 else None
+    del X
+    si = sharded.ShardedIndex(blob, lo, N, storage="bf16", keep_fp32=True)
+    n = args.n_queries
+    qb = [torch.from_numpy(Q[b * n:(b + 1) * n]).cuda() for b in range(max(1, Q.shape[0] // n))]
+    setting, sweep = None, []
+    for ef in (10, 16, 24, 32, 40, 48, 50, 56, 64, 80, 96, 128):
+        ids, _ = si.search(qb[0], args.k, ef, rerank=True)
+        torch.cuda.synchronize()
+        ok = torch.zeros(1, device="cuda")
+        if rank == 0:
+            r = recall_at(ids.cpu().numpy().view(np.uint32), gt[:n])
+            sweep.append((ef, round(r, 5)))
+            ok[0] = float(r >= args.target_recall)
+        dist.broadcast(ok, 0)
+        if ok.item() > 0:
+            setting = {"ef": ef, "rerank": True, "recall": sweep[-1][1] if rank == 0 else None}
+            break
+    if setting is None:
+        raise SystemExit("sharded search never reached the target recall")
+    for i in range(args.warmup):
+        si.search(qb[i % len(qb)], args.k, setting["ef"], rerank=True)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        si.search(qb[i % len(qb)], args.k, setting["ef"], rerank=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    si.close()
+    if rank == 0:
+        out = {"metric": "queries/s at recall@10 >= 0.95, data-sharded search (merged answers)",
+               "value": round(n / (ms / 1e3), 1), "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "strong",
+               "dtype": "f32 arithmetic (bf16 storage, f32 rerank)", "data": "synthetic",
+               "config": {"workload": f"SIFT-shaped {n}-query batch over {N}x128, {world} shard(s) of "
+                                      f"~{N // world} elements, k={args.k}",
+                          "parallelism": f"data-sharded x{world} (all-gather of each shard's k nearest, top-k merge)",
+                          "setting": setting, "sweep": sweep, "shard_build_seconds": round(t_build, 1)}}
+        print(json.dumps(out), flush=True)
+    dist.destroy_process_group()
 
 
 def build_compare(args, log):
