@@ -93,6 +93,11 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 #ifndef HNSW_B16_U
 #define HNSW_B16_U 2
 #endif
+// HNSW_MERGE_BALLOT: a merge with at most 3 candidates finds their places in
+// W by ballots over the entries held in registers instead of a binary search
+#ifndef HNSW_MERGE_BALLOT
+#define HNSW_MERGE_BALLOT 1
+#endif
 // HNSW_MIXED_SUB: for bf16 / f16 rows and squared L2, x - q in one
 // mixed-precision subtraction per coordinate (the 16-bit x taken as it is
 // stored, q in fp32, the difference rounded once to fp32: the same value as
@@ -549,8 +554,9 @@ __device__ int merge_batch(uint64_t* W, int& size, int efp, const uint32_t* ids,
 // written once.  Same result as merge_batch.
 __device__ int merge_small(uint64_t* W, int& size, int efp, const uint32_t* ids, const float* dst, int n,
                            int lane) {
-    const uint64_t w0 = lane < size ? W[lane] : 0ull;
-    const uint64_t w1 = lane + 32 < size ? W[lane + 32] : 0ull;
+    // W's entries lane and lane + 32 (beyond size: all ones, above every key)
+    const uint64_t w0 = lane < size ? W[lane] : ~0ull;
+    const uint64_t w1 = lane + 32 < size ? W[lane + 32] : ~0ull;
     const bool full = size >= efp;
     const uint64_t wlast = size > 0 ? (W[size - 1] >> 1) : 0ull;
     uint64_t k = 0, k1 = 0;
@@ -560,12 +566,32 @@ __device__ int merge_small(uint64_t* W, int& size, int efp, const uint32_t* ids,
         k = mkkey(dst[lane], ids[lane]);
         k1 = k >> 1;
         ok = !(full && k1 > wlast);
-        if (ok) {
-#pragma unroll
-            for (int step = 32; step > 0; step >>= 1)  // entries of W below k1
-                if (lb + step <= size && (W[lb + step - 1] >> 1) < k1) lb += step;
-            if (lb < size && (W[lb] >> 1) == k1) ok = false;  // already in W
+    }
+    const uint32_t cand = __ballot_sync(kFull, ok);
+    if (cand == 0) return INT_MAX;
+#if HNSW_MERGE_BALLOT
+    if (__popc(cand) <= 3) {
+        // few candidates: each one's lower bound and duplicate test by two
+        // ballots over the entries held in registers (keys compared without
+        // the expanded bit: new keys have it clear)
+        const uint64_t m0 = w0 & ~1ull, m1 = w1 & ~1ull;
+        for (uint32_t bits = cand; bits; bits &= bits - 1) {
+            const int sl = __ffs(bits) - 1;
+            const uint64_t ks = __shfl_sync(kFull, k, sl);
+            const int l = __popc(__ballot_sync(kFull, m0 < ks)) + __popc(__ballot_sync(kFull, m1 < ks));
+            const bool dup = __any_sync(kFull, m0 == ks || m1 == ks);  // already in W
+            if (lane == sl) {
+                lb = l;
+                ok = !dup;
+            }
         }
+    } else
+#endif
+    if (ok) {
+#pragma unroll
+        for (int step = 32; step > 0; step >>= 1)  // entries of W below k1
+            if (lb + step <= size && (W[lb + step - 1] >> 1) < k1) lb += step;
+        if (lb < size && (W[lb] >> 1) == k1) ok = false;  // already in W
     }
     const uint32_t surv = __ballot_sync(kFull, ok);
     if (surv == 0) return INT_MAX;
@@ -799,15 +825,16 @@ __global__ void __launch_bounds__(256) __maxnreg__((search_max_regs<ST, TEAM, CP
                 unsigned win_m = 0u;
                 uint32_t win_id = 0u;
                 for (int s = scan; s < size; s += 32) {
+                    // the low word of a key holds the id and the expanded bit
                     const int i = s + lane;
-                    const uint64_t wk = i < size ? W[i] : 1ull;
-                    const bool un = !(wk & 1ull);
+                    const uint32_t wlo = i < size ? reinterpret_cast<const uint32_t*>(W)[2 * i] : 1u;
+                    const bool un = !(wlo & 1u);
                     const unsigned m = __ballot_sync(kFull, un);
                     if (m) {
                         const int b = __ffs(m) - 1;
                         p = s + b;
                         win_m = b < 31 ? (m & (~0u << (b + 1))) : 0u;
-                        win_id = key_id(wk);
+                        win_id = (wlo >> 1) & 0x7fffffffu;
                         break;
                     }
                 }
@@ -852,9 +879,9 @@ __global__ void __launch_bounds__(256) __maxnreg__((search_max_regs<ST, TEAM, CP
                     uint32_t id = win_id;
                     if (!m) {
                         const int i = p + 1 + lane;
-                        const bool un = i < size && !(W[i] & 1ull);
-                        m = __ballot_sync(kFull, un);
-                        id = un ? key_id(W[i]) : 0u;
+                        const uint32_t wlo = i < size ? reinterpret_cast<const uint32_t*>(W)[2 * i] : 1u;
+                        m = __ballot_sync(kFull, !(wlo & 1u));
+                        id = (wlo >> 1) & 0x7fffffffu;
                     }
                     if (m) {
                         nxt_id = __shfl_sync(kFull, id, __ffs(m) - 1);
