@@ -93,10 +93,19 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 #ifndef HNSW_B16_U
 #define HNSW_B16_U 2
 #endif
-// HNSW_MERGE_BALLOT: a merge with at most 3 candidates finds their places in
-// W by ballots over the entries held in registers instead of a binary search
+// HNSW_MERGE_BALLOT: a merge with at most HNSW_MERGE_BALLOT_MAX candidates
+// finds their places in W by ballots over the entries held in registers
+// instead of a binary search
 #ifndef HNSW_MERGE_BALLOT
 #define HNSW_MERGE_BALLOT 1
+#endif
+#ifndef HNSW_MERGE_BALLOT_MAX
+#define HNSW_MERGE_BALLOT_MAX 3
+#endif
+// HNSW_SORT_CHECK: after the rerank, W is sorted only when some adjacent
+// pair is out of order
+#ifndef HNSW_SORT_CHECK
+#define HNSW_SORT_CHECK 1
 #endif
 // HNSW_MIXED_SUB: for bf16 / f16 rows and squared L2, x - q in one
 // mixed-precision subtraction per coordinate (the 16-bit x taken as it is
@@ -570,7 +579,7 @@ __device__ int merge_small(uint64_t* W, int& size, int efp, const uint32_t* ids,
     const uint32_t cand = __ballot_sync(kFull, ok);
     if (cand == 0) return INT_MAX;
 #if HNSW_MERGE_BALLOT
-    if (__popc(cand) <= 3) {
+    if (__popc(cand) <= HNSW_MERGE_BALLOT_MAX) {
         // few candidates: each one's lower bound and duplicate test by two
         // ballots over the entries held in registers (keys compared without
         // the expanded bit: new keys have it clear)
@@ -676,13 +685,19 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 #ifndef HNSW_NARROW_REGS
 #define HNSW_NARROW_REGS 56
 #endif
+// HNSW_STOP_NARROW: the learned-stop build of those instances takes the same
+// budget (the bf16 one then spills 4 bytes, cheaper than 4 fewer warps per SM)
+#ifndef HNSW_STOP_NARROW
+#define HNSW_STOP_NARROW 1
+#endif
 template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP, bool CHECK>
 constexpr int search_max_regs() {
     return (ST == HNSW_F32 && CPL == 4) ? ((STOP || CHECK) ? 80 : 72)
          : (ST == HNSW_FP8E4M3 && U == 8) ? 96
          : (ST == HNSW_F16 && U == 4) ? 80
-         : (!STOP && !CHECK && ((ST == HNSW_BF16 && TEAM == 8 && CPL == 2 && FULL) || TEAM == 2)) ? HNSW_NARROW_REGS
-                                                                                      : 64;
+         : ((!STOP || HNSW_STOP_NARROW) && !CHECK &&
+            ((ST == HNSW_BF16 && TEAM == 8 && CPL == 2 && FULL) || TEAM == 2)) ? HNSW_NARROW_REGS
+                                                                              : 64;
 }
 
 // CHECK: the bounds-checked build (hnsw_search_params.check_bounds): every
@@ -984,7 +999,14 @@ __global__ void __launch_bounds__(256) __maxnreg__((search_max_regs<ST, TEAM, CP
             }
             for (int i = size + lane; i < a.efcap; i += 32) W[i] = ~0ull;
             __syncwarp();
-            warp_sort(W, a.efcap, lane);
+#if HNSW_SORT_CHECK
+            // keys are distinct (distinct ids): W needs no sort when every
+            // adjacent pair is still in order
+            bool unsorted = false;
+            for (int i = lane; i + 1 < size; i += 32) unsorted |= W[i] > W[i + 1];
+            if (__any_sync(kFull, unsorted))
+#endif
+                warp_sort(W, a.efcap, lane);
         }
         const int kq = a.q_kef ? int(__ldg(a.q_kef + qi) & 0xffffu) : a.k;
         const uint64_t obase = a.q_kef ? __ldg(a.q_out + qi) : uint64_t(qi) * uint64_t(a.k);
