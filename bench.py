@@ -719,6 +719,8 @@ def main():
             "timing": f"{args.steps} consecutive {n}-query batches (cycling through {nbat} distinct batches) "
                       f"launched back to back on {max(1, args.streams)} CUDA streams in turn; value = "
                       "queries / timed region; batch_alone_ms = one batch timed alone after an L2 flush",
+            "schedule": "automatic: one launch per batch with deferral (a query whose descent ends nearer "
+                        "than the mean so far has its layer-0 beam run after the input queue is drained)",
             "batch_alone_ms": round(ms_alone, 4),
             "launch_ms_mean": round(launch_ms, 4),
             "form": chosen, "storage": fc["storage"], "rerank": fc["rerank"], "setting": sc,

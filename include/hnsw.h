@@ -263,12 +263,24 @@ typedef struct {
     int32_t stop_period;     /* learned stop / trace: check every stop_period layer-0
                                 expansions (<= 0: 8 for the stop, 4 for traces;
                                 above 65535: HNSW_EINVAL) */
-    int32_t schedule;        /* 0: automatic -- batches larger than four times the kernel's
-                                resident warps run in two passes, the upper-layer descent of all
-                                queries first, then the layer-0 beams in order of
-                                decreasing descent distance (long searches start first,
-                                results unchanged; uses stream-ordered scratch);
-                                1: one pass in input order; 2: always two passes */
+    int32_t schedule;        /* order of the work (results and counters unchanged; both
+                                scheduled forms take stream-ordered scratch, 16 bytes per
+                                query):
+                                0: automatic -- deferral (3) for batches of more than 32
+                                queries, else one pass;
+                                1: one pass in input order;
+                                2: two passes -- the upper-layer descent of all queries
+                                first, then the layer-0 beams in order of decreasing
+                                descent distance;
+                                3: deferral -- one pass in which a query whose descent
+                                ends nearer than the mean of the descents before it is set
+                                aside and its layer-0 beam run once the input queue is
+                                drained, so that the long searches start first.  Its
+                                device-side wait is bounded: a wait that runs out (never
+                                in normal operation) leaves that claim and is reported as
+                                HNSW_ETIMEOUT by this call, when it synchronises (host
+                                buffers), else by the next call on the index that does.
+                                Other values: HNSW_EINVAL */
     int32_t check_bounds;    /* 1: the bounds-checked search -- every element id read from
                                 the graph is checked against N and every upper-row index
                                 against the rows allocated before it is used; a query
@@ -287,6 +299,14 @@ typedef struct {
 hnsw_status hnsw_search_ex(hnsw_index* index, const hnsw_search_params* params,
                            const float* queries, int64_t n, uint32_t* out_ids, float* out_dists,
                            hnsw_query_stats* stats, void* stream);
+
+/* Test hook for the bounded wait of the deferral (schedule 3): while `on` is
+ * non-zero, searches on this index withhold the decision of query 0, so that
+ * claims waiting for the final count of deferred queries run into their limit
+ * (2^20 polls, 0.1 to 1 s), leave, and the call reports HNSW_ETIMEOUT; every query is
+ * still searched and its results are complete.  No device fault and no trap.
+ * Not for production use.  Errors: HNSW_EINVAL (null index). */
+hnsw_status hnsw_debug_hold_decisions(hnsw_index* index, int32_t on);
 
 /* ------------------------------------------------------------------------ */
 /* Learned early stop of the layer-0 beam (an addition: the paper has none)  */

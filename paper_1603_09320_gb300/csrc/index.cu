@@ -173,6 +173,13 @@ hnsw_status upload_index(const void* graph_blob, uint64_t blob_bytes, hnsw_dtype
             dalloc(reinterpret_cast<void**>(&ix->d_work), kWorkSlots * 4) != cudaSuccess) {
             return fail(HNSW_ENOMEM, "hnsw_upload_index: device adjacency");
         }
+        if (cudaHostAlloc(reinterpret_cast<void**>(&ix->h_err), 4, cudaHostAllocMapped | cudaHostAllocPortable) !=
+                cudaSuccess ||
+            cudaHostGetDevicePointer(reinterpret_cast<void**>(&ix->d_err), ix->h_err, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HNSW_ENOMEM, "hnsw_upload_index: error word");
+        }
+        *reinterpret_cast<volatile uint32_t*>(ix->h_err) = 0u;
         HNSW_CUDA_TRY(cudaMemcpyAsync(ix->d_nbr0, nbr0.data(), nbr0.size() * 4, cudaMemcpyHostToDevice, s), "copy nbr0");
         HNSW_CUDA_TRY(cudaMemcpyAsync(ix->d_upoff, upoff.data(), N * 4, cudaMemcpyHostToDevice, s), "copy upoff");
         HNSW_CUDA_TRY(cudaMemcpyAsync(ix->d_nbrU, nbrU.data(), nbrU.size() * 4, cudaMemcpyHostToDevice, s), "copy nbrU");
@@ -247,6 +254,7 @@ extern "C" hnsw_status hnsw_free_index(hnsw_index* ix) {
     for (auto& st : ix->stages)
         if (st.buf) cudaFree(st.buf);
     if (ix->d_vec32 && ix->d_vec32 != ix->d_vec) cudaFree(ix->d_vec32);
+    if (ix->h_err) cudaFreeHost(ix->h_err);
     delete ix;
     return HNSW_OK;
 }

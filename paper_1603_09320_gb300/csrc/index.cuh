@@ -105,6 +105,14 @@ struct hnsw_index {
     int active = 0;
     std::mutex insert_mu;
     int device = 0;
+    // a search kernel whose bounded wait ran out sets this word (host memory
+    // mapped into the device's address space: h_err on the host, d_err on
+    // the device); the next search call that synchronises reads and clears it
+    uint32_t* h_err = nullptr;
+    uint32_t* d_err = nullptr;
+    // test hook (hnsw_debug_hold_decisions): searches withhold one decision
+    // of the deferral, so that its claims wait until their limit runs out
+    std::atomic<int> hold_decisions{0};
 };
 
 namespace hnswgb {

@@ -169,6 +169,20 @@ struct SearchArgs {
     uint64_t* ep_keys;   // [n]
     uint32_t* up_cnt;    // [n][2]: distance evaluations, rows read on layers >= 1
     const uint32_t* order;
+    // deferral (mode 0, null: off): a query whose descent ends nearer than
+    // the mean descent distance of the queries before it is pushed, with its
+    // layer-0 enter key and upper-layer counters, and its beam runs once the
+    // input queue is drained, so that the far (long) searches start first.
+    // dfr_ctl: [0] records pushed, [1] claim tickets taken, [2] error (a
+    // record that never appeared), [3] descents seen, [4] their distance sum
+    // (fp32), [5] input-queue queries past their decision.
+    // dfr_rec[i]: enter key low / high word, counters (rows read on layers
+    // >= 1 << 20 | distance evaluations), query index -- written last, all
+    // ones until then.
+    uint32_t* dfr_ctl;
+    uint4* dfr_rec;  // [n]
+    int dfr_hold;    // test hook: query 0's decision is never counted
+    uint32_t* err;   // the index's error word (host memory mapped on the device)
 };
 
 // ---- keys -----------------------------------------------------------------
@@ -649,6 +663,71 @@ __device__ void warp_sort(uint64_t* a, int n, int lane) {
 }
 
 
+// ---- deferred queries (mode 0) ----------------------------------------------
+// Both run on one lane.  A claim takes the next ticket (one atomic, no
+// retries) and waits for that slot's record -- written by a warp that holds
+// the slot and is running -- or, when every query of the input queue has
+// passed its decision and the slot was never pushed, gives up the ticket.
+// The warps it waits for hold input-queue queries already (the queue is
+// drained before any claim) and decide right after their descent.  The wait
+// is bounded (2^20 polls, 0.1 to 1 s): a record that does not appear by then
+// sets the error word and the claim gives up.
+constexpr int kDeferSpin = 1 << 20;
+constexpr uint32_t kDeferWarmup = 32;  // descents seen before any is deferred
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// A pushed record (its .w = query index), or .w = kNone when none is left.
+__device__ uint4 claim_deferred(const SearchArgs& a) {
+    uint32_t* ctl = a.dfr_ctl;
+    const uint32_t d = atomicAdd(ctl + 1, 1u);
+    if (d >= a.n) return make_uint4(0u, 0u, 0u, kNone);
+    const uint32_t* rw = reinterpret_cast<const uint32_t*>(a.dfr_rec + d);
+    for (int it = 0; it < kDeferSpin; ++it) {
+        const uint32_t q = ld_volatile_u32(rw + 3);
+        if (q != kNone) {
+            __threadfence();
+            return make_uint4(ld_volatile_u32(rw), ld_volatile_u32(rw + 1), ld_volatile_u32(rw + 2), q);
+        }
+        if (ld_volatile_u32(ctl + 5) >= a.n) {  // every decision made: the pushes are final
+            __threadfence();
+            if (d >= ld_volatile_u32(ctl + 0)) return make_uint4(0u, 0u, 0u, kNone);
+        }
+        __nanosleep(128);
+    }
+    atomicExch(ctl + 2, 1u);
+    if (a.err) {
+        *reinterpret_cast<volatile uint32_t*>(a.err) = 1u;
+        __threadfence_system();
+    }
+    return make_uint4(0u, 0u, 0u, kNone);
+}
+
+// Pushes query qi (layer-0 enter key, upper-layer counters) when its descent
+// distance is below the mean of those seen before it; counts the decision
+// (after the record is written) either way and returns whether it pushed.
+__device__ bool maybe_defer(const SearchArgs& a, uint32_t qi, uint64_t cur, uint32_t n_eval, uint32_t n_stepU) {
+    uint32_t* ctl = a.dfr_ctl;
+    const float d1 = key_dist(cur);
+    const uint32_t seen = atomicAdd(ctl + 3, 1u);
+    const float sum = atomicAdd(reinterpret_cast<float*>(ctl + 4), d1);
+    const bool push = seen >= kDeferWarmup && d1 * float(seen) < sum && n_eval < (1u << 20) && n_stepU < (1u << 12);
+    if (push) {
+        const uint32_t s = atomicAdd(ctl + 0, 1u);
+        volatile uint32_t* rw = reinterpret_cast<volatile uint32_t*>(a.dfr_rec + s);
+        rw[0] = uint32_t(cur);
+        rw[1] = uint32_t(cur >> 32);
+        rw[2] = (n_stepU << 20) | n_eval;
+        __threadfence();
+        rw[3] = qi;
+    }
+    __threadfence();
+    if (!(a.dfr_hold && qi == 0)) atomicAdd(ctl + 5, 1u);
+    return push;
+}
+
 // ---- the kernel -------------------------------------------------------------
 // STOP: the build with learned-stop checks and trace recording (the plain
 // search is compiled without them and keeps its smaller register budget).
@@ -677,7 +756,7 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 // threads resident per SM, 36 warps -- where the kernel fits in it without
 // spilling (full bf16 rows of 2 chunks per lane, the 2-lane teams of low-d
 // rows); 64 (8 blocks) for the other narrow ones; more where the rows in
-// flight need them (fp32 128-d: 72, with the stop or bounds checks 80; fp8 with 8 rows
+// flight need them (fp32 128-d: 72; with the stop, the bounds checks or partial rows 80; fp8 with 8 rows
 // per team: 96; f16 with 4 rows per team: 80).  Without an explicit budget
 // the compiler chose budgets that spilled.  Blocks of up to 256 threads are
 // allowed so that large per-warp state (wide beams) can be packed into the
@@ -692,7 +771,7 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 #endif
 template <int ST, int TEAM, int CPL, int U, bool FULL, bool STOP, bool CHECK>
 constexpr int search_max_regs() {
-    return (ST == HNSW_F32 && CPL == 4) ? ((STOP || CHECK) ? 80 : 72)
+    return (ST == HNSW_F32 && CPL == 4) ? ((STOP || CHECK || !FULL) ? 80 : 72)
          : (ST == HNSW_FP8E4M3 && U == 8) ? 96
          : (ST == HNSW_F16 && U == 4) ? 80
          : ((!STOP || HNSW_STOP_NARROW) && !CHECK &&
@@ -728,7 +807,24 @@ __global__ void __launch_bounds__(256) __maxnreg__((search_max_regs<ST, TEAM, CP
         uint32_t qi = 0;
         if (lane == 0) qi = atomicAdd(a.work, 1u);
         qi = __shfl_sync(kFull, qi, 0);
-        if (qi >= a.n) break;
+        // a deferred query taken up again (its enter key and counters parked
+        // in aux words 10-12 until the beam starts)
+        bool resumed = false;
+        if (qi >= a.n) {
+            if (CHECK || !a.dfr_ctl) break;
+            // the input queue is drained: the deferred queries' beams
+            if (lane == 0) {
+                const uint4 r = claim_deferred(a);
+                uint32_t* park = reinterpret_cast<uint32_t*>(aux) + 10;
+                park[0] = r.x;
+                park[1] = r.y;
+                park[2] = r.z;
+                qi = r.w;
+            }
+            qi = __shfl_sync(kFull, qi, 0);
+            if (qi == kNone) break;
+            resumed = true;
+        }
         if (a.mode == 2) qi = __ldg(a.order + qi);
         const float* qp = a.q + uint64_t(qi) * ix.d;
         // per-query k and ef of a grouped launch (k is reread where needed so
@@ -749,7 +845,12 @@ __global__ void __launch_bounds__(256) __maxnreg__((search_max_regs<ST, TEAM, CP
         bool bad = CHECK && ix.N > 0 && !(ix.ep < ix.N);  // bounds-checked build: a bad id or row met
         if (ix.N > 0 && !bad) {
             uint64_t cur = 0;
-            if (a.mode == 2) {  // the descent ran in the first pass
+            if (resumed) {  // the descent ran before the query was deferred
+                const uint32_t* park = reinterpret_cast<const uint32_t*>(aux) + 10;
+                cur = (uint64_t(park[1]) << 32) | park[0];
+                n_eval = park[2] & 0xfffffu;
+                n_stepU = park[2] >> 20;
+            } else if (a.mode == 2) {  // the descent ran in the first pass
                 cur = a.ep_keys[qi];
                 n_eval = a.up_cnt[2 * uint64_t(qi)];
                 n_stepU = a.up_cnt[2 * uint64_t(qi) + 1];
@@ -812,6 +913,11 @@ __global__ void __launch_bounds__(256) __maxnreg__((search_max_regs<ST, TEAM, CP
                 }
                 __syncwarp();
                 continue;
+            }
+            if (!CHECK && a.dfr_ctl && !resumed) {
+                bool deferred = false;
+                if (lane == 0) deferred = maybe_defer(a, qi, cur, n_eval, n_stepU);
+                if (__shfl_sync(kFull, deferred, 0)) continue;  // its beam runs later
             }
             // layer 0 beam (Alg. 2 with ef')
             if (lane == 0) {
@@ -1038,36 +1144,80 @@ __global__ void __launch_bounds__(256) __maxnreg__((search_max_regs<ST, TEAM, CP
 // ---- ordering of the second pass --------------------------------------------
 // Queries whose upper-layer descent ends far from them tend to need more
 // layer-0 expansions; starting them first shortens the tail of the batch
-// (longest-first list scheduling).  One block sorts a chunk of up to
-// kSortChunk queries by descending descent distance (bitonic sort of
-// (~ord(d1), query) keys in shared memory); chunks are sorted independently.
+// (longest-first list scheduling).  The order need not be exact: one block
+// takes a chunk of up to kSortChunk queries and places them by a counting
+// sort into kOrderBuckets buckets spanning the chunk's range of descent
+// distances (linear in the distances' ordered bit patterns, so about
+// logarithmic in the distances), farthest first; chunks are ordered
+// independently.  Block barriers only (no spin-waits); launched with one
+// thread per bucket.
 constexpr int kSortChunk = 16384;
+constexpr int kOrderBuckets = 1024;
+static_assert(kOrderBuckets == 1024, "the prefix sum takes one bucket per thread of a 1024-thread block");
 
 __global__ void __launch_bounds__(1024) order_by_descent(const uint64_t* __restrict__ ep_keys, uint32_t n,
                                                         uint32_t* __restrict__ order) {
-    extern __shared__ __align__(16) uint64_t sk[];
+    __shared__ uint32_t hist[kOrderBuckets];
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t range[2];
     const uint32_t base = blockIdx.x * uint32_t(kSortChunk);
     const uint32_t m = min(uint32_t(kSortChunk), n - base);
-    uint32_t P = 1;
-    while (P < m) P <<= 1;
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
-        sk[i] = i < m ? ((uint64_t(~uint32_t(ep_keys[base + i] >> 32)) << 32) | uint64_t(base + i)) : ~0ull;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int i = t; i < kOrderBuckets; i += blockDim.x) hist[i] = 0u;
+    if (t == 0) {
+        range[0] = ~0u;
+        range[1] = 0u;
+    }
     __syncthreads();
-    for (uint32_t kk = 2; kk <= P; kk <<= 1)
-        for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                const uint32_t q = i ^ j;
-                if (q > i) {
-                    const uint64_t x = sk[i], y = sk[q];
-                    if ((x > y) == ((i & kk) == 0)) {
-                        sk[i] = y;
-                        sk[q] = x;
-                    }
-                }
-            }
-            __syncthreads();
+    // the chunk's range of ordered distance bits (the high word of a key)
+    uint32_t lo = ~0u, hi = 0u;
+    for (uint32_t i = t; i < m; i += blockDim.x) {
+        const uint32_t v = uint32_t(ep_keys[base + i] >> 32);
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+    lo = __reduce_min_sync(kFull, lo);
+    hi = __reduce_max_sync(kFull, hi);
+    if (lane == 0) {
+        atomicMin(&range[0], lo);
+        atomicMax(&range[1], hi);
+    }
+    __syncthreads();
+    lo = range[0];
+    hi = range[1];
+    const uint64_t span = uint64_t(hi - lo) + 1u;  // >= 1 (m >= 1)
+    // bucket of a key: 0 for the farthest enter point
+    auto bucket = [&](uint32_t i) {
+        const uint32_t v = uint32_t(ep_keys[base + i] >> 32);
+        return uint32_t((uint64_t(hi - v) * uint64_t(kOrderBuckets)) / span);
+    };
+    for (uint32_t i = t; i < m; i += blockDim.x) atomicAdd(&hist[bucket(i)], 1u);
+    __syncthreads();
+    // exclusive prefix sum of the histogram (one entry per thread)
+    const uint32_t x = t < kOrderBuckets ? hist[t] : 0u;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = int(blockDim.x) >> 5;
+        uint32_t w = lane < nw ? wsum[lane] : 0u, wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += y;
         }
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) order[base + i] = uint32_t(sk[i]);
+        if (lane < nw) wsum[lane] = wi - w;  // exclusive over warps
+    }
+    __syncthreads();
+    if (t < kOrderBuckets) hist[t] = wsum[wid] + inc - x;
+    __syncthreads();
+    // scatter: the slots of a bucket go to its queries in any order
+    for (uint32_t i = t; i < m; i += blockDim.x) order[base + atomicAdd(&hist[bucket(i)], 1u)] = base + i;
 }
 
 // ---- host side --------------------------------------------------------------
@@ -1208,7 +1358,8 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
                                uint32_t* ids, float* dists, hnsw_query_stats* stats, cudaStream_t s,
                                uint32_t* work, const StopModel* stop, int mode, uint64_t* ep_keys,
                                uint32_t* up_cnt, const uint32_t* order, const uint32_t* q_kef = nullptr,
-                               const uint64_t* q_out = nullptr, const DevIndex* view = nullptr) {
+                               const uint64_t* q_out = nullptr, const DevIndex* view = nullptr,
+                               uint32_t* dfr_ctl = nullptr, uint4* dfr_rec = nullptr) {
     const DevIndex D = view ? *view : dev_snapshot(ix);
     KernelChoice kc;
     if (p.check_bounds) {
@@ -1237,6 +1388,10 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
     a.ep_keys = ep_keys;
     a.up_cnt = up_cnt;
     a.order = order;
+    a.dfr_ctl = p.check_bounds ? nullptr : dfr_ctl;
+    a.dfr_rec = dfr_rec;
+    a.dfr_hold = ix->hold_decisions.load() ? 1 : 0;
+    a.err = ix->d_err;
     if (stop) {
         a.stop = static_cast<const StopDev*>(stop->stop);
         a.stop_logit = stop->logit_threshold;
@@ -1325,16 +1480,42 @@ uint32_t take_work_slots(hnsw_index* ix) {
     return (ix->work_next.fetch_add(1) % uint32_t(kWorkSlots / 2)) * 2u;
 }
 
-// Resident warps of the search kernel (about 7 blocks per SM x 4 warps x SMs).
-// Measured on SIFT-shaped 1M, the two-pass order gains a few percent only when
-// a batch is several times larger than this (at 10,000 queries the separate
-// descent pass costs more than the ordering saves), so the automatic choice
-// uses it above four times this count.
-uint32_t resident_warps(const hnsw_index* ix) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return uint32_t(sms) * 28u;
+// The two-pass scratch comes from the device's default stream-ordered pool,
+// which by default hands freed memory back at every synchronisation, so that
+// the next call maps it again.  This process keeps up to 256 MB of it cached
+// (an attribute of the process's pool, nothing of the device's settings).
+#ifndef HNSW_POOL_KEEP
+#define HNSW_POOL_KEEP 1
+#endif
+void keep_pool_memory() {
+#if HNSW_POOL_KEEP
+    static std::mutex mu;
+    static std::map<int, bool> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = 256ull << 20;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+#endif
+}
+
+// Reads and clears the index's error word (set by a kernel whose bounded wait
+// ran out); call after the work that may set it has completed.
+bool take_device_error(hnsw_index* ix) {
+    if (!ix->h_err) return false;
+    volatile uint32_t* w = ix->h_err;
+    if (*w == 0u) return false;
+    *w = 0u;
+    return true;
 }
 
 // One launch over the queries of several requests of one index (the
@@ -1371,6 +1552,7 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     if ((p->ef > p->k ? p->ef : p->k) > kMaxEf) return fail(HNSW_EINVAL, "hnsw_search: ef' above 1024");
     if (p->visited_log2 != 0 && (p->visited_log2 < 5 || p->visited_log2 > 15))
         return fail(HNSW_EINVAL, "hnsw_search: visited_log2 outside [5,15]");
+    if (p->schedule < 0 || p->schedule > 3) return fail(HNSW_EINVAL, "hnsw_search: schedule outside [0,3]");
     if (p->rerank && !ix->dev.vec32) return fail(HNSW_EINVAL, "hnsw_search: rerank needs the fp32 copy");
     if (p->stop_period > 65535) return fail(HNSW_EINVAL, "hnsw_search: stop_period above 65535");
     if (n == 0) return HNSW_OK;
@@ -1461,17 +1643,39 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     // schedule: 0 automatic (two passes when the batch exceeds the resident
     // warps), 1 one pass in input order, 2 always two passes
     const DevIndex snap = dev_snapshot(ix);  // both passes search the same version
-    const bool two = snap.N > 0 && !p->check_bounds &&
-                     (p->schedule == 2 || (p->schedule == 0 && uint64_t(n) > 4ull * resident_warps(ix)));
+    const bool two = snap.N > 0 && !p->check_bounds && p->schedule == 2;
+    const bool defer = !two && snap.N > 0 && !p->check_bounds &&
+                       (p->schedule == 3 || (p->schedule == 0 && uint64_t(n) > kDeferWarmup));
     hnsw_status r = HNSW_OK;
-    if (!two) {
+    if (!two && !defer) {
         r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 0, nullptr, nullptr, nullptr,
                                nullptr, nullptr, &snap);
+        if (r != HNSW_OK) return r;
+    } else if (defer) {
+        // stream-ordered scratch: control words (64 bytes, zero) and one
+        // 16-byte record per query (all ones until written)
+        void* scr = nullptr;
+        const size_t bc = 256, br = al256(size_t(n) * 16);
+        keep_pool_memory();
+        e = cudaMallocAsync(&scr, bc + br, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HNSW_ENOMEM, "hnsw_search: scheduling scratch");
+        }
+        uint32_t* ctl = static_cast<uint32_t*>(scr);
+        uint4* rec = reinterpret_cast<uint4*>(static_cast<char*>(scr) + bc);
+        if ((e = cudaMemsetAsync(ctl, 0, bc, s)) != cudaSuccess || (e = cudaMemsetAsync(rec, 0xff, br, s)) != cudaSuccess)
+            r = fail(HNSW_ECUDA, std::string("hnsw_search: memset: ") + cudaGetErrorString(e));
+        if (r == HNSW_OK)
+            r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 0, nullptr, nullptr,
+                                   nullptr, nullptr, nullptr, &snap, ctl, rec);
+        cudaFreeAsync(scr, s);
         if (r != HNSW_OK) return r;
     } else {
         // stream-ordered scratch: enter keys [n] u64, upper counters [n][2] u32, order [n] u32
         void* scr = nullptr;
         const size_t bk = al256(size_t(n) * 8), bc = al256(size_t(n) * 8), bo = al256(size_t(n) * 4);
+        keep_pool_memory();
         e = cudaMallocAsync(&scr, bk + bc + bo, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -1483,14 +1687,8 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
         r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 1, keys, cnt, nullptr, nullptr,
                                nullptr, &snap);
         if (r == HNSW_OK) {
-            r = raise_smem_limit(reinterpret_cast<const void*>(order_by_descent), size_t(kSortChunk) * 8,
-                                 "hnsw_search: order");
-            if (r != HNSW_OK) {
-                cudaFreeAsync(scr, s);
-                return r;
-            }
             const unsigned chunks = unsigned((uint64_t(n) + kSortChunk - 1) / kSortChunk);
-            order_by_descent<<<chunks, 1024, kSortChunk * 8, s>>>(keys, uint32_t(n), ord);
+            order_by_descent<<<chunks, 1024, 0, s>>>(keys, uint32_t(n), ord);
             e = cudaGetLastError();
             if (e != cudaSuccess) r = fail(HNSW_ECUDA, std::string("hnsw_search: order: ") + cudaGetErrorString(e));
         }
@@ -1509,7 +1707,15 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     if (!dq || !di || !dd || !ds) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(HNSW_ECUDA, std::string("hnsw_search: ") + cudaGetErrorString(e));
+        if (take_device_error(ix))
+            return fail(HNSW_ETIMEOUT, "hnsw_search: a bounded device-side wait ran out (this or an earlier call)");
     }
+    return HNSW_OK;
+}
+
+extern "C" hnsw_status hnsw_debug_hold_decisions(hnsw_index* ix, int32_t on) {
+    if (!ix) return fail(HNSW_EINVAL, "hnsw_debug_hold_decisions: null index");
+    ix->hold_decisions.store(on ? 1 : 0);
     return HNSW_OK;
 }
 

@@ -105,6 +105,7 @@ def lib():
             "hnsw_get_index_info": (i32, [vp, C.POINTER(IndexInfo)]),
             "hnsw_search": (i32, [vp, vp, i64, i32, i32, vp, vp, vp]),
             "hnsw_search_ex": (i32, [vp, C.POINTER(SearchParams), vp, i64, vp, vp, vp, vp]),
+            "hnsw_debug_hold_decisions": (i32, [vp, i32]),
             "hnsw_last_error": (C.c_char_p, []),
             "hnsw_set_stop_model": (i32, [vp, vp, vp]),
             "hnsw_clear_stop_model": (i32, [vp]),
@@ -249,6 +250,11 @@ class Index:
 
     def _refresh(self) -> None:
         _check(lib().hnsw_get_index_info(self.h, C.byref(self.info)))
+
+    def debug_hold_decisions(self, on: bool) -> None:
+        """hnsw_debug_hold_decisions (test hook): while on, the deferral's
+        bounded wait runs out and the search reports ETIMEOUT."""
+        _check(lib().hnsw_debug_hold_decisions(self.h, int(bool(on))))
 
     def reserve(self, capacity: int, stream=None) -> None:
         """hnsw_reserve: room for `capacity` elements (incremental insertion)."""

@@ -1,6 +1,11 @@
-"""Two-pass scheduling (descent of all queries, then the layer-0 beams in
-order of decreasing descent distance) changes only the order of work: ids,
-distances and counters equal the one-pass search and the oracle."""
+"""Scheduling changes only the order of work: ids, distances and counters
+equal the one-pass search in input order and the oracle.
+
+* two passes: the descent of all queries, then the layer-0 beams in order of
+  decreasing descent distance;
+* deferral: one pass in which a query whose descent ends nearer than the
+  mean so far is set aside and its beam run after the input queue is
+  drained."""
 import numpy as np
 import pytest
 
@@ -11,24 +16,74 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("storage,keep,rerank", [("f32", False, False), ("bf16", True, True)])
-def test_two_pass_equals_one_pass_and_oracle(storage, keep, rerank):
+def test_schedules_equal_one_pass_and_oracle(storage, keep, rerank):
     import torch
     from paper_1603_09320_gb300 import build, hnsw
     build.build()
     g, X, blob = oracle_graph("sift", 20_000)
     ix = hnsw.Index(blob, storage, keep_fp32=keep)
-    Q = synth.queries("sift", 20_000)  # above 16,384: two sort chunks
+    Q = synth.queries("sift", 20_000)  # above 16,384: two ordering chunks
     q = torch.from_numpy(Q).cuda()
     a = ix.search(q, 10, 48, rerank=rerank, stats=True, schedule=1)
-    b = ix.search(q, 10, 48, rerank=rerank, stats=True, schedule=2)
-    c = ix.search(q, 10, 48, rerank=rerank, stats=True)  # automatic: one pass at this size
+    others = [ix.search(q, 10, 48, rerank=rerank, stats=True, schedule=s) for s in (2, 3, 0)]
+    others += [ix.search(q[:n], 10, 48, rerank=rerank, stats=True, schedule=3) for n in (1, 33, 5000)]
     torch.cuda.synchronize()
-    for x, y in ((a, b), (a, c)):
-        assert torch.equal(x[0], y[0]) and torch.equal(x[1], y[1]) and torch.equal(x[2][:, 1:3], y[2][:, 1:3])
-    ids = b[0].cpu().numpy().view(np.uint32)
-    ds = b[1].cpu().numpy()
+    ev_diff = []
+    for y in others:
+        m = y[0].shape[0]
+        assert torch.equal(a[0][:m], y[0]) and torch.equal(a[1][:m], y[1])
+        assert torch.equal(a[2][:m, 1:3], y[2][:, 1:3])  # layer-0 expansions, upper rows read
+        # evaluations: the lossy visited set may forget an id when two lanes
+        # store into one slot at once, and evaluate it again (results unchanged)
+        ev_diff.append(int((a[2][:m, 0] - y[2][:, 0]).abs().max()))
+    assert max(ev_diff) <= 16, ev_diff
+    ids = a[0].cpu().numpy().view(np.uint32)
+    ds = a[1].cpu().numpy()
     for i in range(0, 20_000, 997):
         oi, od = g.knn_search(Q[i], 10, 48)
         np.testing.assert_array_equal(ids[i], oi)
         np.testing.assert_array_equal(ds[i].astype(np.float64), od)
+    ix.close()
+
+
+def test_deferral_with_the_learned_stop_and_host_buffers():
+    # the stop instance and the host-memory path take the same deferral
+    import torch
+    from paper_1603_09320_gb300 import build, hnsw
+    build.build()
+    g, X, blob = oracle_graph("sift", 20_000)
+    ix = hnsw.Index(blob, "bf16", keep_fp32=True)
+    Q = synth.queries("sift", 12_000)
+    a = ix.search(Q, 10, 48, rerank=True, schedule=1)
+    b = ix.search(Q, 10, 48, rerank=True, schedule=3)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    ix.close()
+
+
+def test_deferral_wait_runs_out_and_is_reported():
+    # the test hook withholds one decision: the claims that wait for the final
+    # count of deferred queries run into their limit (0.1 to 1 s), leave, and the
+    # call reports ETIMEOUT -- no fault, the context stays usable, and every
+    # query was still searched
+    import torch
+    from paper_1603_09320_gb300 import build, hnsw
+    build.build()
+    g, X, blob = oracle_graph("sift", 20_000)
+    ix = hnsw.Index(blob, "bf16", keep_fp32=True)
+    Q = synth.queries("sift", 12_000)
+    a = ix.search(Q, 10, 48, rerank=True, schedule=1)
+    ix.debug_hold_decisions(True)
+    ids = torch.empty((12_000, 10), dtype=torch.int32, device="cuda")
+    ds = torch.empty((12_000, 10), dtype=torch.float32, device="cuda")
+    ix.search_into(torch.from_numpy(Q).cuda(), 10, 48, ids, ds, rerank=True, schedule=3)  # asynchronous
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ids.cpu().numpy().view(np.uint32), a[0])
+    np.testing.assert_array_equal(ds.cpu().numpy(), a[1])
+    with pytest.raises(hnsw.HnswError) as e:  # the next call that synchronises reports it
+        ix.search(Q[:100], 10, 48, rerank=True, schedule=1)
+    assert e.value.status == 5
+    ix.debug_hold_decisions(False)
+    b = ix.search(Q, 10, 48, rerank=True)  # reported once, then clear
+    np.testing.assert_array_equal(a[0], b[0])
     ix.close()
