@@ -266,7 +266,7 @@ typedef struct {
     int32_t schedule;        /* order of the work (results and counters unchanged; both
                                 scheduled forms take stream-ordered scratch, 16 bytes per
                                 query):
-                                0: automatic -- deferral (3) for batches of more than 32
+                                0: automatic -- deferral (3) for batches of 33 to 2^24
                                 queries, else one pass;
                                 1: one pass in input order;
                                 2: two passes -- the upper-layer descent of all queries

@@ -674,6 +674,9 @@ __device__ void warp_sort(uint64_t* a, int n, int lane) {
 // sets the error word and the claim gives up.
 constexpr int kDeferSpin = 1 << 20;
 constexpr uint32_t kDeferWarmup = 32;  // descents seen before any is deferred
+// the automatic schedule defers in batches of up to 2^24 queries (256 MB of
+// records); in larger ones the tail is a small part of the batch
+constexpr uint64_t kDeferAutoMax = 1ull << 24;
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
     return *reinterpret_cast<const volatile uint32_t*>(p);
@@ -1645,7 +1648,8 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
     const DevIndex snap = dev_snapshot(ix);  // both passes search the same version
     const bool two = snap.N > 0 && !p->check_bounds && p->schedule == 2;
     const bool defer = !two && snap.N > 0 && !p->check_bounds &&
-                       (p->schedule == 3 || (p->schedule == 0 && uint64_t(n) > kDeferWarmup));
+                       (p->schedule == 3 ||
+                        (p->schedule == 0 && uint64_t(n) > kDeferWarmup && uint64_t(n) <= kDeferAutoMax));
     hnsw_status r = HNSW_OK;
     if (!two && !defer) {
         r = launch_search_mode(ix, *p, q, uint32_t(n), ids, dists, st, s, work, smp, 0, nullptr, nullptr, nullptr,
