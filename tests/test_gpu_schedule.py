@@ -47,17 +47,27 @@ def test_schedules_equal_one_pass_and_oracle(storage, keep, rerank):
 
 
 def test_deferral_with_the_learned_stop_and_host_buffers():
-    # the stop instance and the host-memory path take the same deferral
+    # the stop instance (any fixed network: its decisions depend only on the
+    # query's own search) and the host-memory path take the same deferral
     import torch
-    from paper_1603_09320_gb300 import build, hnsw
+    from paper_1603_09320_gb300 import build, hnsw, stopnet
     build.build()
     g, X, blob = oracle_graph("sift", 20_000)
     ix = hnsw.Index(blob, "bf16", keep_fp32=True)
+    ix.set_stop_model(np.array([0] * 6 + [1] * 6, np.float32), stopnet.init_weights(5))
     Q = synth.queries("sift", 12_000)
-    a = ix.search(Q, 10, 48, rerank=True, schedule=1)
-    b = ix.search(Q, 10, 48, rerank=True, schedule=3)
-    np.testing.assert_array_equal(a[0], b[0])
-    np.testing.assert_array_equal(a[1], b[1])
+    q = torch.from_numpy(Q).cuda()
+    kw = dict(rerank=True, stats=True, stop_threshold=0.5, stop_period=8)
+    a = ix.search(q, 10, 64, schedule=1, **kw)
+    b = ix.search(q, 10, 64, schedule=3, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert torch.equal(a[2][:, 1:], b[2][:, 1:])  # expansions, upper rows, flags (stopped early)
+    assert int(((a[2][:, 3] & 2) != 0).sum()) > 0  # the network does stop searches
+    c = ix.search(Q, 10, 48, rerank=True, schedule=1)
+    d = ix.search(Q, 10, 48, rerank=True, schedule=3)
+    np.testing.assert_array_equal(c[0], d[0])
+    np.testing.assert_array_equal(c[1], d[1])
     ix.close()
 
 
