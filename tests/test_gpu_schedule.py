@@ -57,7 +57,7 @@ def test_deferral_with_the_learned_stop_and_host_buffers():
     ix.set_stop_model(np.array([0] * 6 + [1] * 6, np.float32), stopnet.init_weights(5))
     Q = synth.queries("sift", 12_000)
     q = torch.from_numpy(Q).cuda()
-    kw = dict(rerank=True, stats=True, stop_threshold=0.5, stop_period=8)
+    kw = dict(rerank=True, stats=True, stop_threshold=0.2, stop_period=8)
     a = ix.search(q, 10, 64, schedule=1, **kw)
     b = ix.search(q, 10, 64, schedule=3, **kw)
     torch.cuda.synchronize()
