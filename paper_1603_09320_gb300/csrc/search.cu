@@ -1483,10 +1483,11 @@ uint32_t take_work_slots(hnsw_index* ix) {
     return (ix->work_next.fetch_add(1) % uint32_t(kWorkSlots / 2)) * 2u;
 }
 
-// The two-pass scratch comes from the device's default stream-ordered pool,
-// which by default hands freed memory back at every synchronisation, so that
-// the next call maps it again.  This process keeps up to 256 MB of it cached
-// (an attribute of the process's pool, nothing of the device's settings).
+// The scheduling scratch (two passes, deferral) comes from the device's
+// default stream-ordered pool, which by default hands freed memory back at
+// every synchronisation, so that the next call maps it again.  This process
+// keeps up to 256 MB of it cached (an attribute of the process's pool,
+// nothing of the device's settings).
 #ifndef HNSW_POOL_KEEP
 #define HNSW_POOL_KEEP 1
 #endif
@@ -1643,8 +1644,8 @@ extern "C" hnsw_status hnsw_search_ex(hnsw_index* ix, const hnsw_search_params* 
         sm.period = p->stop_period > 0 ? p->stop_period : 8;
         smp = &sm;
     }
-    // schedule: 0 automatic (two passes when the batch exceeds the resident
-    // warps), 1 one pass in input order, 2 always two passes
+    // schedule: 0 automatic (deferral for 33 to 2^24 queries, else one pass),
+    // 1 one pass in input order, 2 two passes, 3 deferral
     const DevIndex snap = dev_snapshot(ix);  // both passes search the same version
     const bool two = snap.N > 0 && !p->check_bounds && p->schedule == 2;
     const bool defer = !two && snap.N > 0 && !p->check_bounds &&
