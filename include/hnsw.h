@@ -256,7 +256,11 @@ typedef struct {
     int32_t ef;
     int32_t rerank;          /* 1: recompute fp32 distances of all ef' final candidates
                                 from the fp32 copy and return the top k of those */
-    int32_t visited_log2;    /* log2 of visited-set slots per query, 0 = automatic */
+    int32_t visited_log2;    /* log2 of visited-set slots per query; 0 = automatic: the
+                                largest set from 2^8 up to 8-16 slots per beam entry
+                                (at most 2^12) that keeps as many warps resident as
+                                2^8 slots do (the set may forget elements, which only
+                                repeats evaluations; results are the same at any size) */
     float stop_threshold;    /* learned stop: in (0,1) stop the layer-0 beam when the stop
                                 network's sigmoid exceeds it (needs hnsw_set_stop_model);
                                 <= 0 or >= 1: off, the plain search */

@@ -1349,10 +1349,12 @@ bool block_choice(KernelFn fn, size_t warp_smem, int& warps, int& per_sm) {
 
 }  // namespace
 
+// Upper bound of the automatic visited set: about 8-16 slots per beam entry,
+// 1,024 to 4,096 slots (a layer-0 search evaluates some 10-30 x ef'
+// elements); the launch takes the largest size up to it that costs no
+// resident warps, and not below kMinAutoHlog.
+constexpr int kMinAutoHlog = 8;
 int auto_visited_log2(int efp) {
-    // about 8-16 slots per beam entry, 1,024 to 4,096 slots: a layer-0 search
-    // evaluates some 10-30 x ef' elements, but a larger set costs occupancy
-    // and overflow only repeats evaluations
     int l = ceil_log2(uint64_t(efp) * 8);
     return l < 10 ? 10 : (l > 12 ? 12 : l);
 }
@@ -1379,7 +1381,6 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
     a.k = p.k;
     a.efp = p.ef > p.k ? p.ef : p.k;
     a.efcap = 1 << ceil_log2(uint64_t(a.efp < 32 ? 32 : a.efp));
-    a.hlog = p.visited_log2 > 0 ? p.visited_log2 : auto_visited_log2(a.efp);
     a.rerank = p.rerank;
     a.out_ids = ids;
     a.out_dists = dists;
@@ -1406,24 +1407,51 @@ hnsw_status launch_search_mode(hnsw_index* ix, const hnsw_search_params& p, cons
         a.tr_max = stop->tr_max;
     }
     const bool stop_build = stop != nullptr && stop->period > 0;
-    // per-warp layout (every piece a multiple of 16 bytes)
-    const size_t hbytes = (size_t(1) << a.hlog) * 4, row32 = size_t(D.row_chunks32) * 16;
-    size_t per_warp = size_t(a.efcap) * 8 + hbytes + kMaxDeg * 12 + 64;
-    // merge_batch (W above 64 entries, or a neighbour batch above 32) and
-    // the stop check's scratch use ck and lbs
-    if (stop_build || a.efcap > 64 || D.s0 > 32) {
-        a.off_ck = int(per_warp);
-        a.off_lbs = int(per_warp + kMaxDeg * 8);
-        per_warp += kMaxDeg * 12;
-    } else {
-        a.off_ck = a.off_lbs = 0;
+    const size_t row32 = size_t(D.row_chunks32) * 16;
+    // per-warp layout with a visited set of 2^hl slots (every piece a
+    // multiple of 16 bytes); sets the offsets in t, returns the bytes
+    auto layout = [&](int hl, SearchArgs& t) {
+        const size_t hbytes = (size_t(1) << hl) * 4;
+        size_t per_warp = size_t(t.efcap) * 8 + hbytes + kMaxDeg * 12 + 64;
+        // merge_batch (W above 64 entries, or a neighbour batch above 32) and
+        // the stop check's scratch use ck and lbs
+        if (stop_build || t.efcap > 64 || D.s0 > 32) {
+            t.off_ck = int(per_warp);
+            t.off_lbs = int(per_warp + kMaxDeg * 8);
+            per_warp += kMaxDeg * 12;
+        } else {
+            t.off_ck = t.off_lbs = 0;
+        }
+        if (!p.rerank || hbytes >= row32) {
+            t.off_qs = t.efcap * 8;  // the visited set's bytes
+        } else {
+            t.off_qs = int(per_warp);
+            per_warp += row32;
+        }
+        return per_warp;
+    };
+    int hl = p.visited_log2 > 0 ? p.visited_log2 : auto_visited_log2(a.efp);
+    if (p.visited_log2 <= 0) {
+        // automatic: the largest set, down to 2^8 slots, that keeps as many
+        // warps resident as the smallest does.  A forgotten element only
+        // costs a repeated evaluation, while the warps resident decide how
+        // much of the gathers' latency is hidden (a wide beam's state is
+        // bound by shared memory, a narrow one's by registers).
+        SearchArgs t = a;
+        const size_t most = std::min<size_t>(227 * 1024, size_t(8) * layout(hl, t));
+        const hnsw_status st = raise_smem_limit(reinterpret_cast<const void*>(kc.fn), most, "search");
+        if (st != HNSW_OK) return st;
+        int w0 = 0, b0 = 0;
+        if (!block_choice(kc.fn, layout(kMinAutoHlog, t), w0, b0))
+            return fail(HNSW_ECUDA, "search: occupancy query failed");
+        for (; hl > kMinAutoHlog; --hl) {
+            const size_t pw = layout(hl, t);
+            int w = 0, b = 0;
+            if (pw <= 227 * 1024 && block_choice(kc.fn, pw, w, b) && w * b >= w0 * b0) break;
+        }
     }
-    if (!p.rerank || hbytes >= row32) {
-        a.off_qs = a.efcap * 8;  // the visited set's bytes
-    } else {
-        a.off_qs = int(per_warp);
-        per_warp += row32;
-    }
+    a.hlog = hl;
+    const size_t per_warp = layout(hl, a);
     a.warp_smem = int(per_warp);
     if (size_t(a.warp_smem) > 227 * 1024)
         return fail(HNSW_EINVAL, "search: ef/visited set too large for shared memory");
