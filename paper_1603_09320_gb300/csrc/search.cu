@@ -93,6 +93,11 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 #ifndef HNSW_B16_U
 #define HNSW_B16_U 2
 #endif
+// HNSW_FP8_U: rows a team of fp8 rows keeps in flight (2: 64 registers,
+// 32 warps per SM; 8 took 96 registers, 20 warps, and ran 1.7x slower)
+#ifndef HNSW_FP8_U
+#define HNSW_FP8_U 2
+#endif
 // HNSW_MERGE_BALLOT: a merge with at most HNSW_MERGE_BALLOT_MAX candidates
 // finds their places in W by ballots over the entries held in registers
 // instead of a binary search
@@ -760,7 +765,7 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 // spilling (full bf16 rows of 2 chunks per lane, the 2-lane teams of low-d
 // rows); 64 (8 blocks) for the other narrow ones; more where the rows in
 // flight need them (fp32 128-d: 72; with the stop, the bounds checks or partial rows 80; fp8 with 8 rows
-// per team: 96; f16 with 4 rows per team: 80).  Without an explicit budget
+// per team, when HNSW_FP8_U asks for them: 96; f16 with 4 rows per team: 80).  Without an explicit budget
 // the compiler chose budgets that spilled.  Blocks of up to 256 threads are
 // allowed so that large per-warp state (wide beams) can be packed into the
 // shared memory of an SM (see the launch).
@@ -1262,7 +1267,7 @@ bool choose_kernel(int storage, uint32_t chunks, bool stop, KernelChoice& kc) {
             if (chunks <= 64) { kc = pick<HNSW_F16, 32, 2, 1>(chunks, stop); return true; }
             return false;
         case HNSW_FP8E4M3:
-            if (chunks <= 8) { kc = pick<HNSW_FP8E4M3, 8, 1, 8>(chunks, stop); return true; }
+            if (chunks <= 8) { kc = pick<HNSW_FP8E4M3, 8, 1, HNSW_FP8_U>(chunks, stop); return true; }
             if (chunks <= 32) { kc = pick<HNSW_FP8E4M3, 32, 1, 1>(chunks, stop); return true; }
             return false;
     }
