@@ -98,6 +98,15 @@ constexpr int kMaxDeg = 64;  // neighbour slots scored per expansion
 #ifndef HNSW_FP8_U
 #define HNSW_FP8_U 2
 #endif
+// HNSW_F16_U: the same for f16 rows (2: 64 registers; 4 took 80 registers
+// and ran 1.2x slower).  HNSW_F16_NARROW: full f16 rows at the narrow budget
+// (56, 36 warps): -1.5% overlapped but +8% for a batch alone, so off
+#ifndef HNSW_F16_U
+#define HNSW_F16_U 2
+#endif
+#ifndef HNSW_F16_NARROW
+#define HNSW_F16_NARROW 0
+#endif
 // HNSW_MERGE_BALLOT: a merge with at most HNSW_MERGE_BALLOT_MAX candidates
 // finds their places in W by ballots over the entries held in registers
 // instead of a binary search
@@ -765,7 +774,7 @@ HNSW_STOP_FN float stop_check(const StopDev* model, const uint64_t* W, int size,
 // spilling (full bf16 rows of 2 chunks per lane, the 2-lane teams of low-d
 // rows); 64 (8 blocks) for the other narrow ones; more where the rows in
 // flight need them (fp32 128-d: 72; with the stop, the bounds checks or partial rows 80; fp8 with 8 rows
-// per team, when HNSW_FP8_U asks for them: 96; f16 with 4 rows per team: 80).  Without an explicit budget
+// per team, when HNSW_FP8_U asks for them: 96; f16 with 4 rows per team, when HNSW_F16_U asks: 80).  Without an explicit budget
 // the compiler chose budgets that spilled.  Blocks of up to 256 threads are
 // allowed so that large per-warp state (wide beams) can be packed into the
 // shared memory of an SM (see the launch).
@@ -783,7 +792,7 @@ constexpr int search_max_regs() {
          : (ST == HNSW_FP8E4M3 && U == 8) ? 96
          : (ST == HNSW_F16 && U == 4) ? 80
          : ((!STOP || HNSW_STOP_NARROW) && !CHECK &&
-            ((ST == HNSW_BF16 && TEAM == 8 && CPL == 2 && FULL) || TEAM == 2)) ? HNSW_NARROW_REGS
+            (((ST == HNSW_BF16 || (ST == HNSW_F16 && HNSW_F16_NARROW)) && TEAM == 8 && CPL == 2 && FULL) || TEAM == 2)) ? HNSW_NARROW_REGS
                                                                               : 64;
 }
 
@@ -1263,7 +1272,7 @@ bool choose_kernel(int storage, uint32_t chunks, bool stop, KernelChoice& kc) {
             return false;
         case HNSW_F16:
             if (chunks <= 2) { kc = pick<HNSW_F16, 2, 1, 2>(chunks, stop); return true; }
-            if (chunks <= 16) { kc = pick<HNSW_F16, 8, 2, 4>(chunks, stop); return true; }
+            if (chunks <= 16) { kc = pick<HNSW_F16, 8, 2, HNSW_F16_U>(chunks, stop); return true; }
             if (chunks <= 64) { kc = pick<HNSW_F16, 32, 2, 1>(chunks, stop); return true; }
             return false;
         case HNSW_FP8E4M3:

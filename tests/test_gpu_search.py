@@ -118,9 +118,11 @@ def test_lossy_visited_set_same_result(H, vlog):
 
 
 @pytest.mark.parametrize("storage,keep,rerank", [("f32", False, False), ("bf16", False, False),
-                                                 ("bf16", True, True), ("f32", True, True)])
+                                                 ("bf16", True, True), ("f32", True, True),
+                                                 ("f16", False, False), ("f16", True, True)])
 def test_sift_shaped_bit_exact(H, storage, keep, rerank):
-    # integer coordinates 0..255: bf16 stores them exactly, so bf16 is lossless
+    # integer coordinates 0..255: bf16 and f16 store them exactly, so both are
+    # lossless (f16 rows of d = 128 take the 8-lane-team instance)
     g, X, blob = oracle_graph("sift", 20_000)
     Q = synth.queries("sift", 500)
     gi, gd = gpu_search(H, blob, Q, 10, 64, storage=storage, keep=keep, rerank=rerank)
